@@ -1,0 +1,231 @@
+/*
+ * fif.h -- C ABI of the GB300-native Fisher Information Field library (libfif.so).
+ *
+ * The method (Zhang & Scaramuzza, arXiv 2008.03324): precompute, once, a per-voxel
+ * positional information factor from a sparse landmark map (Sec. VI-A-1,
+ * Eq. general_info_pif), then recover the Fisher information of any camera pose in
+ * constant time by contracting the factor with the camera's optical-axis monomials
+ * (Eq. fim_separation, Eq. general_info_query) and reducing it to an information metric
+ * (Sec. IV).  The direct point-cloud FIM (Eq. cost_info) is provided as the baseline.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Ownership: the caller allocates and frees every buffer, host or device, including the
+ *   field storage and the build workspace.  The library never allocates device memory.
+ * - Pointers named d_* are device pointers (cudaMalloc or torch tensors on the current
+ *   device); all others are host pointers.  Device pointers must be 16-byte aligned.
+ * - Asynchrony: compute entry points enqueue kernels on `stream` and return at once.
+ *   Their return code reports argument and launch errors only; results are valid after
+ *   the stream has been synchronised.  A NULL stream is the legacy default stream.
+ * - Errors: every call returns FIF_OK (0) or a negative FIF_E* code; fif_status_str()
+ *   names it.  Device-side failures never trap: per-pose problems go to the optional
+ *   per-pose status array, and a bounded wait that runs out sets the library's device
+ *   error word (fif_device_error()).
+ * - Pose layout: float32[m][7] = (tx, ty, tz, qw, qx, qy, qz); the quaternion gives R_wc
+ *   (camera to world), t = camera centre in the world.  Non-unit quaternions are
+ *   renormalised.
+ * - Perturbation order: xi = (rho, phi), translation first, as in [-I3, [p]x]
+ *   (Eq. jac_pose_global).
+ * - A symmetric 6x6 matrix is stored as its 21 upper-triangular entries in row-major
+ *   order: (0,0) (0,1) .. (0,5) (1,1) .. (1,5) (2,2) .. (5,5).
+ * - Thread safety: calls on different fields may run concurrently; concurrent builds
+ *   into the same field race.
+ */
+#ifndef FIF_H_
+#define FIF_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define FIF_API __attribute__((visibility("default")))
+#else
+#define FIF_API
+#endif
+
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st* fif_stream_t;
+
+/* ---- return codes ------------------------------------------------------------------ */
+#define FIF_OK 0
+#define FIF_EINVAL (-1)    /* a NULL pointer, a non-positive size, an unknown flag       */
+#define FIF_ESIZE (-2)     /* a caller buffer is smaller than the call needs             */
+#define FIF_EALIGN (-3)    /* a device pointer is not 16-byte aligned                    */
+#define FIF_ECUDA (-4)     /* a CUDA launch or runtime call failed                       */
+#define FIF_ETIMEOUT (-5)  /* a bounded device wait ran out (see fif_device_error)       */
+#define FIF_EIO (-6)       /* file could not be opened, read or written                  */
+#define FIF_EFORMAT (-7)   /* file is not a field of this version / size / layout        */
+#define FIF_ERANGE (-8)    /* a size exceeds a fixed maximum of the call                 */
+
+/* ---- per-pose status bits (d_status) ------------------------------------------------ */
+#define FIF_POSE_OUTSIDE 1   /* position outside the lattice box; clamped onto it        */
+#define FIF_POSE_QUAT 2      /* |q|^2 differed from 1 by more than 1e-3; renormalised    */
+#define FIF_POSE_NOT_PD 4    /* the FIM is not positive definite (sign <= 0 or l_min <= 0)*/
+#define FIF_POSE_NAN 8       /* non-finite pose; outputs are NaN                         */
+
+/* ---- storage of the field ------------------------------------------------------------ */
+#define FIF_STORAGE_F32 0    /* float32, 216 elements (864 B) per node                  */
+#define FIF_STORAGE_BF16 1   /* bfloat16 (round to nearest even), 224 elements (448 B)    */
+
+/* ---- query flags ---------------------------------------------------------------------- */
+#define FIF_Q_TRILINEAR 0x0  /* interpolate over the 8 surrounding nodes (default)        */
+#define FIF_Q_NEAREST 0x1    /* nearest node only (the paper's "FIM from nearest voxel")  */
+#define FIF_Q_CAMERA 0x0     /* FIM in the camera frame, local perturbation (default)     */
+#define FIF_Q_WORLD 0x2      /* FIM in the world frame, global perturbation about origin  */
+#define FIF_Q_TRACE 0x10     /* compute trace            (metrics column 0)               */
+#define FIF_Q_LOGDET 0x20    /* compute log|det| + sign  (metrics column 1, d_sign)       */
+#define FIF_Q_LMIN 0x40      /* compute lambda_min       (metrics column 2)               */
+#define FIF_Q_METRICS 0x70   /* all three                                                 */
+
+/* Lattice of voxel nodes: node (i, j, k) sits at origin + res * (i, j, k), i < nx, j < ny,
+ * k < nz, each count >= 2.  Node index n = i + nx * (j + ny * k). */
+typedef struct fif_grid {
+    float origin[3];
+    float res;
+    int32_t nx, ny, nz;
+} fif_grid;
+
+/* Parameters of the method.
+ * half_fov, v_alpha: the quadratic visibility v(theta) = k2 cos^2 + k1 cos + k0 meets
+ *   v(0) = 1, v(pi) = 0, v(half_fov) = v_alpha (Eq. quadratic_conditions, Sec. V-B-1).
+ * r_min, r_max: the landmarks seen from a position x are those with
+ *   r_min < |p - x| <= r_max (the set V_t of Sec. V; the paper leaves its choice to the
+ *   map, this library uses a range shell).  The test is taken in single precision:
+ *   dx = p - x per axis, n2 = (dx*dx + dy*dy) + dz*dz, each operation rounded, compared
+ *   with (float)(r_min*r_min) and (float)(r_max*r_max).
+ * sigma: bearing noise std (Eq. fim_gaussian); every FIM is scaled by 1/sigma^2.
+ * bin_size: edge of the cubic cells used to cull landmarks during the build (metres,
+ *   0 selects 1.0).  It changes speed only, never results. */
+typedef struct fif_params {
+    double half_fov;
+    double v_alpha;
+    double r_min;
+    double r_max;
+    double sigma;
+    float bin_size;
+    int32_t reserved;
+} fif_params;
+
+/* Pinhole camera for the exact visibility of the point-cloud baseline
+ * (Eq. exact_vis_func): a landmark is visible iff its camera-frame depth z > 0 and
+ * fx*x + cx*z lies in [0, width*z) and fy*y + cy*z lies in [0, height*z), all in single
+ * precision with one rounding per operation, i.e. its pixel lies inside the image. */
+typedef struct fif_pinhole {
+    float fx, fy, cx, cy;
+    int32_t width, height;
+} fif_pinhole;
+
+/* A field: the lattice, the method's parameters and the caller-owned device storage.
+ * Storage layout: node n occupies elements [n*stride, (n+1)*stride) of `coeffs`; element
+ * n*stride + 21*k + e holds entry e (upper-triangular, row-major) of the 6x6 matrix
+ * C_k = sum_i v_p(u_i)[k] I_i, k indexing the monomials of Eq. quad_vis_component,
+ * v_p = [u1^2, u2^2, u3^2, u1 u2, u1 u3, u2 u3, u1, u2, u3, 1], u_i the unit bearing
+ * from the node to landmark i, I_i its information (Eq. global_fim_eq) with the
+ * rotational part of the perturbation taken about the node itself (the paper's world
+ * frame moved to the node: C^world = M_c^T C M_c, M_c = [[I, -[c]x], [0, I]]).
+ * Elements 210 .. stride-1 are zero.  k[] = (k0, k1, k2) is filled by fif_field_init. */
+typedef struct fif_field {
+    fif_grid grid;
+    fif_params params;
+    int32_t storage;   /* FIF_STORAGE_F32 or FIF_STORAGE_BF16                      */
+    int32_t stride;    /* elements per node                                         */
+    void* coeffs;      /* device storage, caller-owned                              */
+    size_t bytes;      /* size of `coeffs` in bytes                                 */
+    double k[3];       /* k0, k1, k2                                                */
+} fif_field;
+
+/* Library version (major*10000 + minor*100 + patch). */
+FIF_API int32_t fif_version(void);
+
+/* Static name of a return code. */
+FIF_API const char* fif_status_str(int32_t code);
+
+/* Bytes of field storage for `grid` with the given storage type (0 on a bad argument). */
+FIF_API size_t fif_field_bytes(const fif_grid* grid, int32_t storage);
+
+/* Fill *field: validate grid and params, solve (k0, k1, k2) from Eq. quadratic_conditions
+ * in double precision, and bind the caller's device storage d_coeffs of `bytes` bytes
+ * (at least fif_field_bytes()).  Host only; does not touch the storage. */
+FIF_API int32_t fif_field_init(fif_field* field, const fif_grid* grid, const fif_params* params,
+                       int32_t storage, void* d_coeffs, size_t bytes);
+
+/* Bytes of device workspace fif_build() needs for n landmarks (0 on a bad argument). */
+FIF_API size_t fif_build_workspace_bytes(const fif_field* field, int64_t n_landmarks);
+
+/* Build the field (Sec. VI-A-1, Eq. general_info_pif): for every node c,
+ *   C_k(c) = sum over landmarks with r_min < |p_i - c| <= r_max of v_p(u_i)[k] * I_i.
+ * d_landmarks: float32[n][3] world positions.  d_workspace: at least
+ * fif_build_workspace_bytes(field, n) bytes, contents on entry ignored.  Sums are taken
+ * in single precision with compensated (Kahan) accumulation over blocks of landmarks;
+ * the summation order is fixed by the input order, so equal inputs give bitwise equal
+ * fields.  Overwrites the whole storage.  n may be 0 (the field becomes zero). */
+FIF_API int32_t fif_build(fif_field* field, const float* d_landmarks, int64_t n, void* d_workspace,
+                  size_t workspace_bytes, fif_stream_t stream);
+
+/* Query m poses (Sec. VI-A-1, Eq. fim_separation, Eq. general_info_query):
+ *   I(T) = sum_k v_r(z)[k] * C_k(t),  z = R_wc e3 (the optical axis),
+ * v_r = [k2 z1^2, k2 z2^2, k2 z3^2, 2 k2 z1 z2, 2 k2 z1 z3, 2 k2 z2 z3, k1 z1, k1 z2, k1 z3, k0]
+ * with C_k(t) interpolated trilinearly from the 8 nodes around t (or taken from the
+ * nearest node), expressed in the camera frame (Ad^T I_world Ad, the local perturbation)
+ * or the world frame, then reduced to the metrics selected in `flags`.
+ * Outputs (each optional, NULL to skip):
+ *   d_fim      float32[m][21]  the 6x6 FIM, upper triangle
+ *   d_metrics  float64[m][3]   trace, log|det|, lambda_min (unselected columns untouched)
+ *   d_sign     int8[m]         sign of det (+1, -1, 0)
+ *   d_status   int32[m]        FIF_POSE_* bits
+ * Trace is summed in single precision; log|det| comes from a double-precision LDL^T
+ * (LU with pivoting when it breaks down) of the FIM, and lambda_min from a
+ * single-precision Jacobi eigenvector refined by a double-precision Rayleigh quotient.
+ * Positions outside the lattice are clamped onto it. */
+FIF_API int32_t fif_query(const fif_field* field, const float* d_poses, int64_t m, int32_t flags,
+                  float* d_fim, double* d_metrics, int8_t* d_sign, int32_t* d_status,
+                  fif_stream_t stream);
+
+/* Adjoint of fif_query for the metrics (FIF_Q_CAMERA or FIF_Q_WORLD, trilinear):
+ *   d_grad_pose[i] = sum_c d_grad_metrics[i][c] * d metric_c(T_i) / d(t, phi)
+ * with t the world position and phi a right (camera-frame) so(3) perturbation
+ * R <- R exp(phi^).  d_fim must hold the FIM that fif_query wrote for the same poses,
+ * field and flags.  d_grad_metrics float64[m][3] (trace, log|det|, lambda_min weights; a
+ * zero weight skips that metric), d_grad_pose float32[m][6] = (dt_x, dt_y, dt_z, dphi_x,
+ * dphi_y, dphi_z).  lambda_min's derivative assumes a simple smallest eigenvalue.  Poses
+ * clamped onto the lattice get a zero derivative along the clamped axes. */
+FIF_API int32_t fif_query_backward(const fif_field* field, const float* d_poses, int64_t m, int32_t flags,
+                           const float* d_fim, const double* d_grad_metrics, float* d_grad_pose,
+                           fif_stream_t stream);
+
+/* Direct point-cloud FIM (Sec. IV, Eq. cost_info) -- the baseline the field replaces:
+ *   I(T) = sum over landmarks with r_min < |p - t| <= r_max and exact pinhole visibility
+ *          (Eq. exact_vis_func) of I_T(p)
+ * over all n landmarks for each of m poses, in the frame selected by `flags`
+ * (FIF_Q_CAMERA / FIF_Q_WORLD), with the same optional outputs and metrics as fif_query
+ * (the status bit FIF_POSE_OUTSIDE is never set).  params supplies r_min, r_max, sigma. */
+FIF_API int32_t fif_pointcloud_fim(const float* d_landmarks, int64_t n, const fif_params* params,
+                           const fif_pinhole* camera, const float* d_poses, int64_t m,
+                           int32_t flags, float* d_fim, double* d_metrics, int8_t* d_sign,
+                           int32_t* d_status, fif_stream_t stream);
+
+/* Save the field to a file: a fixed header (magic, version, grid, params, storage,
+ * stride, FNV-1a checksum of the payload) followed by the raw storage.  Synchronises
+ * `stream` and copies through `host_staging` (at least field->bytes bytes, caller-owned;
+ * NULL uses pageable copies). */
+FIF_API int32_t fif_field_save(const fif_field* field, const char* path, void* host_staging,
+                       fif_stream_t stream);
+
+/* Load a field saved by fif_field_save into caller device storage d_coeffs (bytes at least
+ * the saved size); fills *field.  Verifies magic, version, sizes and checksum.  Synchronises
+ * `stream`. */
+FIF_API int32_t fif_field_load(fif_field* field, const char* path, void* d_coeffs, size_t bytes,
+                       void* host_staging, fif_stream_t stream);
+
+/* Read (and if reset != 0 clear) the library's device error word on the current device:
+ * 0 when no bounded device wait has run out since the last reset.  Synchronises `stream`. */
+FIF_API int32_t fif_device_error(int32_t* out_code, int32_t reset, fif_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FIF_H_ */

@@ -1,0 +1,491 @@
+// build.cu -- Fisher Information Field build (sm_103a).
+//
+// Sec. VI-A-1 / Eq. general_info_pif of the paper: for every voxel node c
+//   C_k(c) = sum_{i : r_min < |p_i - c| <= r_max} v_p(u_i)[k] I_i,   k = 0..9,
+// with u_i the unit bearing from c to landmark i, v_p the monomials of
+// Eq. quad_vis_component and I_i the rotation-invariant information of one bearing
+// (Eq. global_fim_eq) taken about the node itself:
+//   I_i = sigma^-2 [[P/n^2, -[u]x/n], [[u]x/n, P]],  P = I - u u^T,  n = |p_i - c|.
+//
+// Kernels
+//  bin_*      counting sort of the landmarks into cubic bins (deterministic order inside a
+//             bin: by input index), so a brick of nodes reads only the landmarks whose bins
+//             come within r_max of it, as contiguous runs.
+//  build      one CTA = a brick of 8 x 4 x 4 nodes, one thread = one register-resident
+//             node.  Thread 0 streams the brick's candidate landmarks through a 3-slot ring
+//             of shared-memory tiles with bulk copies (cp.async.bulk + mbarrier); all 128
+//             threads read each landmark as a shared-memory broadcast.
+//
+// Arithmetic per (node, landmark): every entry of v_p[k] * I_i is a polynomial in u of
+// degree <= 4 times 1/n^2, 1/n or 1.  Because |u| = 1, multiplying by (u.u)^m raises any
+// term to degree 3 or 4 (2 or 3 for 1/n), so all 210 entries are fixed integer combinations
+// of 66 moments
+//   sum u^a / n^2 (|a| = 4, 3),  sum u^a / n (|a| = 3, 2),  sum u^a (|a| = 4, 3),
+// and the hot loop accumulates only those 66 (31 monomials + 66 FMA/FADD per pair).
+// Accumulation is compensated: a block of up to 64 pairs is summed in registers, then the
+// block sum is added to a Kahan (sum, compensation) pair held in shared memory.  The
+// epilogue expands the 66 moments into the 210 stored coefficients.
+#include "fif_common.cuh"
+#include "fif_internal.h"
+
+#include <cmath>
+
+namespace fif {
+
+namespace {
+
+constexpr int kBX = 8, kBY = 4, kBZ = 4;
+constexpr int kThreads = kBX * kBY * kBZ;  // 128
+constexpr int kTile = 256;                  // landmarks per tile
+constexpr int kSlots = 3;
+constexpr int kBlock = 64;                  // pairs per register block (Kahan granularity)
+constexpr int kMaxRuns = 2048;
+constexpr int kMom = 66;
+
+// monomial exponent tables (order fixed by the hot loop)
+__device__ __constant__ int8_t kMon2[6][3] = {{2, 0, 0}, {0, 2, 0}, {0, 0, 2}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1}};
+__device__ __constant__ int8_t kMon3[10][3] = {{3, 0, 0}, {0, 3, 0}, {0, 0, 3}, {2, 1, 0}, {2, 0, 1},
+                                               {1, 2, 0}, {0, 2, 1}, {1, 0, 2}, {0, 1, 2}, {1, 1, 1}};
+__device__ __constant__ int8_t kMon4[15][3] = {{4, 0, 0}, {0, 4, 0}, {0, 0, 4}, {3, 1, 0}, {3, 0, 1},
+                                               {1, 3, 0}, {0, 3, 1}, {1, 0, 3}, {0, 1, 3}, {2, 2, 0},
+                                               {2, 0, 2}, {0, 2, 2}, {2, 1, 1}, {1, 2, 1}, {1, 1, 2}};
+// v_p monomials of Eq. quad_vis_component
+__device__ __constant__ int8_t kVp[10][3] = {{2, 0, 0}, {0, 2, 0}, {0, 0, 2}, {1, 1, 0}, {1, 0, 1},
+                                             {0, 1, 1}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {0, 0, 0}};
+// moment blocks: base index of (power of 1/n, degree)
+constexpr int kS4n2 = 0, kS3n2 = 15, kS3n1 = 25, kS2n1 = 35, kS4n0 = 41, kS3n0 = 56;
+
+// ------------------------------------------------------------------------------------
+// binning
+// ------------------------------------------------------------------------------------
+__global__ void fill_i32_kernel(int* p, int64_t n, int v) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+__device__ __forceinline__ int bin_of(const BinGrid& bg, float x, float y, float z) {
+    const int ix = (int)floorf((x - bg.lo[0]) * bg.inv_size);
+    const int iy = (int)floorf((y - bg.lo[1]) * bg.inv_size);
+    const int iz = (int)floorf((z - bg.lo[2]) * bg.inv_size);
+    if (!(ix >= 0 && ix < bg.n[0] && iy >= 0 && iy < bg.n[1] && iz >= 0 && iz < bg.n[2])) return -1;
+    return ix + bg.n[0] * (iy + bg.n[1] * iz);
+}
+
+__global__ void bin_count_kernel(const float* __restrict__ lm, int64_t n, BinGrid bg, int* __restrict__ binof,
+                                  int* __restrict__ count, unsigned long long* __restrict__ stats) {
+    int dropped = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float x = lm[3 * i], y = lm[3 * i + 1], z = lm[3 * i + 2];
+        int b = (isfinite(x) && isfinite(y) && isfinite(z)) ? bin_of(bg, x, y, z) : -1;
+        binof[i] = b;
+        if (b >= 0) atomicAdd(&count[b], 1);
+        else ++dropped;
+    }
+    if (dropped) atomicAdd(&stats[2], (unsigned long long)dropped);
+}
+
+// exclusive scan of count[0..nb) into start[0..nb], then count <- 0 (reused as cursor)
+__global__ void __launch_bounds__(1024) bin_scan_kernel(int* __restrict__ count, int* __restrict__ start, int nb) {
+    __shared__ int warp_sums[32];
+    const int tid = threadIdx.x;
+    const int per = (nb + 1023) / 1024;
+    const int b0 = min(nb, tid * per), b1 = min(nb, b0 + per);
+    int local = 0;
+    for (int b = b0; b < b1; ++b) local += count[b];
+    // block-wide exclusive scan of `local`
+    int v = local;
+    const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    if (lane == 31) warp_sums[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        int w = warp_sums[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += u;
+        }
+        warp_sums[lane] = w;
+    }
+    __syncthreads();
+    int run = v - local + (warp > 0 ? warp_sums[warp - 1] : 0);
+    for (int b = b0; b < b1; ++b) {
+        start[b] = run;
+        run += count[b];
+        count[b] = 0;
+    }
+    if (tid == 1023) start[nb] = run;
+}
+
+__global__ void bin_scatter_kernel(const float* __restrict__ lm, int64_t n, const int* __restrict__ binof,
+                                   const int* __restrict__ start, int* __restrict__ cursor, float4* __restrict__ sorted) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int b = binof[i];
+        if (b < 0) continue;
+        const int pos = start[b] + atomicAdd(&cursor[b], 1);
+        sorted[pos] = make_float4(lm[3 * i], lm[3 * i + 1], lm[3 * i + 2], __int_as_float((int)i));
+    }
+}
+
+// insertion sort of every bin by input index (makes the summation order deterministic)
+__global__ void bin_sort_kernel(float4* __restrict__ sorted, const int* __restrict__ start, int nb) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+        const int s = start[b], e = start[b + 1];
+        for (int i = s + 1; i < e; ++i) {
+            const float4 v = sorted[i];
+            const int key = __float_as_int(v.w);
+            int j = i - 1;
+            while (j >= s && __float_as_int(sorted[j].w) > key) {
+                sorted[j + 1] = sorted[j];
+                --j;
+            }
+            sorted[j + 1] = v;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// the brick kernel
+// ------------------------------------------------------------------------------------
+struct BuildSmem {
+    float hi[kMom][kThreads];
+    float lo[kMom][kThreads];
+    float4 tile[kSlots][kTile];
+    int2 runs[kMaxRuns];
+    int tile_count[kSlots];
+    int nruns;
+    uint64_t bars[kSlots];
+};
+
+// sum u^a / n^p for a stored degree (|a| = 4 or 3 for p = 0, 2; 3 or 2 for p = 1)
+__device__ float moment_direct(const float* hs, const float* ls, int tid, int p, int ex, int ey, int ez) {
+    const int deg = ex + ey + ez;
+    int base, cnt;
+    const int8_t(*tab)[3];
+    if (deg == 4) { tab = kMon4; cnt = 15; base = (p == 2) ? kS4n2 : kS4n0; }
+    else if (deg == 3) { tab = kMon3; cnt = 10; base = (p == 2) ? kS3n2 : (p == 1) ? kS3n1 : kS3n0; }
+    else { tab = kMon2; cnt = 6; base = kS2n1; }
+    for (int i = 0; i < cnt; ++i)
+        if (tab[i][0] == ex && tab[i][1] == ey && tab[i][2] == ez) {
+            const int idx = base + i;
+            return hs[idx * kThreads + tid] - ls[idx * kThreads + tid];
+        }
+    return 0.f;
+}
+
+// sum u^a / n^p for any |a| <= 4: lower degrees are raised with u.u = 1 (one or two levels)
+__device__ float moment(const float* hs, const float* ls, int tid, int p, int ex, int ey, int ez) {
+    const int top = (p == 1) ? 3 : 4;
+    if (ex + ey + ez >= top - 1) return moment_direct(hs, ls, tid, p, ex, ey, ez);
+    float s = 0.f;
+    for (int c = 0; c < 3; ++c) {
+        const int a0 = ex + (c == 0 ? 2 : 0), a1 = ey + (c == 1 ? 2 : 0), a2 = ez + (c == 2 ? 2 : 0);
+        if (a0 + a1 + a2 >= top - 1) {
+            s += moment_direct(hs, ls, tid, p, a0, a1, a2);
+        } else {
+            for (int d = 0; d < 3; ++d)
+                s += moment_direct(hs, ls, tid, p, a0 + (d == 0 ? 2 : 0), a1 + (d == 1 ? 2 : 0), a2 + (d == 2 ? 2 : 0));
+        }
+    }
+    return s;
+}
+
+__device__ __forceinline__ void kahan_merge(float* hs, float* ls, int idx, float x) {
+    const float s = hs[idx], c = ls[idx];
+    const float y = x - c;
+    const float t = s + y;
+    ls[idx] = (t - s) - y;
+    hs[idx] = t;
+}
+
+__global__ void __launch_bounds__(kThreads, 2) build_kernel(BuildArgs a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    BuildSmem& S = *reinterpret_cast<BuildSmem*>(smem_raw);
+    const int tid = threadIdx.x;
+
+    // brick of nodes
+    const int nbx = (a.nx + kBX - 1) / kBX, nby = (a.ny + kBY - 1) / kBY;
+    const int brick = blockIdx.x;
+    const int bxi = brick % nbx, byi = (brick / nbx) % nby, bzi = brick / (nbx * nby);
+    const int i0 = bxi * kBX, j0 = byi * kBY, k0 = bzi * kBZ;
+    const int ti = tid & 7, tj = (tid >> 3) & 3, tk = tid >> 5;
+    const int ni = i0 + ti, nj = j0 + tj, nk = k0 + tk;
+    const bool valid = ni < a.nx && nj < a.ny && nk < a.nz;
+    const float cx = __fadd_rn(a.ox, __fmul_rn(a.res, (float)ni));
+    const float cy = __fadd_rn(a.oy, __fmul_rn(a.res, (float)nj));
+    const float cz = __fadd_rn(a.oz, __fmul_rn(a.res, (float)nk));
+    // brick box over its valid nodes
+    const float blo[3] = {a.ox + a.res * i0, a.oy + a.res * j0, a.oz + a.res * k0};
+    const float bhi[3] = {a.ox + a.res * min(i0 + kBX - 1, a.nx - 1), a.oy + a.res * min(j0 + kBY - 1, a.ny - 1),
+                          a.oz + a.res * min(k0 + kBZ - 1, a.nz - 1)};
+
+    for (int idx = tid; idx < kMom * kThreads; idx += kThreads) {
+        (&S.hi[0][0])[idx] = 0.f;
+        (&S.lo[0][0])[idx] = 0.f;
+    }
+
+    // ---- enumerate candidate runs: one bin row (y, z) per entry ----
+    const BinGrid& bg = a.bg;
+    const float rc = a.rcull, rc2 = rc * rc;
+    const int ry0 = max(0, (int)floorf((blo[1] - rc - bg.lo[1]) * bg.inv_size));
+    const int ry1 = min(bg.n[1] - 1, (int)floorf((bhi[1] + rc - bg.lo[1]) * bg.inv_size));
+    const int rz0 = max(0, (int)floorf((blo[2] - rc - bg.lo[2]) * bg.inv_size));
+    const int rz1 = min(bg.n[2] - 1, (int)floorf((bhi[2] + rc - bg.lo[2]) * bg.inv_size));
+    const int nry = max(0, ry1 - ry0 + 1), nrz = max(0, rz1 - rz0 + 1);
+    // the host sizes bins so a brick never touches more than kMaxRuns rows; if that ever
+    // failed the field would be wrong, so report it instead of truncating silently
+    if (nry * nrz > kMaxRuns && tid == 0) set_error(a.err, FIF_ERANGE);
+    const int nrows = min(nry * nrz, kMaxRuns);
+    const int* startp = reinterpret_cast<const int*>(a.ws + a.lay.start);
+    for (int r = tid; r < nrows; r += kThreads) {
+        const int ry = ry0 + r % nry, rz = rz0 + r / nry;
+        const float ylo = bg.lo[1] + ry * bg.size, yhi = ylo + bg.size;
+        const float zlo = bg.lo[2] + rz * bg.size, zhi = zlo + bg.size;
+        const float dy = fmaxf(0.f, fmaxf(ylo - bhi[1], blo[1] - yhi));
+        const float dz = fmaxf(0.f, fmaxf(zlo - bhi[2], blo[2] - zhi));
+        const float d2 = dy * dy + dz * dz;
+        int2 run = make_int2(0, 0);
+        if (d2 <= rc2) {
+            const float rx = sqrtf(rc2 - d2);
+            const int bx0 = max(0, (int)floorf((blo[0] - rx - bg.lo[0]) * bg.inv_size));
+            const int bx1 = min(bg.n[0] - 1, (int)floorf((bhi[0] + rx - bg.lo[0]) * bg.inv_size));
+            if (bx1 >= bx0) {
+                const int rowb = bg.n[0] * (ry + bg.n[1] * rz);
+                run = make_int2(startp[rowb + bx0], startp[rowb + bx1 + 1]);
+            }
+        }
+        S.runs[r] = run;
+    }
+    if (tid == 0) {
+        S.nruns = nrows;
+        for (int s = 0; s < kSlots; ++s) mbar_init(&S.bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    // ---- producer state (thread 0 only) ----
+    const float4* sorted = reinterpret_cast<const float4*>(a.ws + a.lay.sorted);
+    int prod_run = 0, prod_off = 0;
+    auto produce = [&](int slot) {
+        // fill one tile from the run list; an empty tile marks the end
+        uint64_t* bar = &S.bars[slot];
+        int cnt = 0;
+        while (cnt < kTile && prod_run < S.nruns) {
+            const int2 run = S.runs[prod_run];
+            const int s0 = run.x + prod_off;
+            const int take = min(run.y - s0, kTile - cnt);
+            if (take > 0) {
+                asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)),
+                             "r"((uint32_t)take * 16u)
+                             : "memory");
+                bulk_g2s(&S.tile[slot][cnt], sorted + s0, (uint32_t)take * 16u, bar);
+                cnt += take;
+                prod_off += take;
+            }
+            if (run.x + prod_off >= run.y) {
+                ++prod_run;
+                prod_off = 0;
+            }
+        }
+        S.tile_count[slot] = cnt;
+        mbar_arrive(bar);
+    };
+    if (tid == 0) {
+        fence_proxy_async();
+        for (int s = 0; s < kSlots; ++s) produce(s);
+    }
+
+    // ---- consume ----
+    const float rmin2 = a.rmin2, rmax2 = a.rmax2;
+    float acc[kMom];
+#pragma unroll
+    for (int i = 0; i < kMom; ++i) acc[i] = 0.f;
+    float* hs = &S.hi[0][0];
+    float* ls = &S.lo[0][0];
+    unsigned int in_pairs = 0;
+    unsigned long long cand = 0;
+    bool ok = true;
+    for (int it = 0;; ++it) {
+        const int slot = it % kSlots;
+        const uint32_t par = (uint32_t)((it / kSlots) & 1);
+        const bool late = !mbar_wait_bounded(&S.bars[slot], par);
+        if (__syncthreads_or(late)) {  // every thread takes the same exit
+            ok = false;
+            if (tid == 0) set_error(a.err, FIF_ETIMEOUT);
+            break;
+        }
+        const int cnt = S.tile_count[slot];
+        if (cnt == 0) break;
+        cand += cnt;
+        const float4* tile = S.tile[slot];
+        for (int b0 = 0; b0 < cnt; b0 += kBlock) {
+            const int b1 = min(cnt, b0 + kBlock);
+#pragma unroll 2
+            for (int l = b0; l < b1; ++l) {
+                const float4 L = tile[l];
+                const float dx = __fsub_rn(L.x, cx), dy = __fsub_rn(L.y, cy), dz = __fsub_rn(L.z, cz);
+                const float n2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+                const bool in = (n2 > rmin2) && (n2 <= rmax2);
+                in_pairs += in ? 1u : 0u;
+                const float r = rsqrtf(n2);
+                const float inv_n = in ? r : 0.f;
+                const float x = dx * inv_n, y = dy * inv_n, z = dz * inv_n;
+                const float w2 = inv_n * inv_n;
+                const float xx = x * x, yy = y * y, zz = z * z, xy = x * y, xz = x * z, yz = y * z;
+                const float m3[10] = {xx * x, yy * y, zz * z, xx * y, xx * z, yy * x, yy * z, zz * x, zz * y, xy * z};
+                const float m4[15] = {xx * xx, yy * yy, zz * zz, xx * xy, xx * xz, yy * xy, yy * yz, zz * xz,
+                                      zz * yz, xx * yy, xx * zz, yy * zz, xx * yz, yy * xz, zz * xy};
+                const float m2[6] = {xx, yy, zz, xy, xz, yz};
+#pragma unroll
+                for (int i = 0; i < 15; ++i) acc[kS4n2 + i] = fmaf(m4[i], w2, acc[kS4n2 + i]);
+#pragma unroll
+                for (int i = 0; i < 10; ++i) acc[kS3n2 + i] = fmaf(m3[i], w2, acc[kS3n2 + i]);
+#pragma unroll
+                for (int i = 0; i < 10; ++i) acc[kS3n1 + i] = fmaf(m3[i], inv_n, acc[kS3n1 + i]);
+#pragma unroll
+                for (int i = 0; i < 6; ++i) acc[kS2n1 + i] = fmaf(m2[i], inv_n, acc[kS2n1 + i]);
+#pragma unroll
+                for (int i = 0; i < 15; ++i) acc[kS4n0 + i] += m4[i];
+#pragma unroll
+                for (int i = 0; i < 10; ++i) acc[kS3n0 + i] += m3[i];
+            }
+            // compensated merge of the block sums
+#pragma unroll
+            for (int i = 0; i < kMom; ++i) {
+                kahan_merge(hs, ls, i * kThreads + tid, acc[i]);
+                acc[i] = 0.f;
+            }
+        }
+        __syncthreads();  // everyone is done with this slot
+        if (tid == 0) {
+            fence_proxy_async();
+            produce(slot);
+        }
+    }
+    // statistics
+    {
+        unsigned long long* stats = reinterpret_cast<unsigned long long*>(a.ws + a.lay.stats);
+        unsigned long long v = valid ? in_pairs : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((tid & 31) == 0 && v) atomicAdd(&stats[0], v);
+        if (tid == 0) {
+            int nvalid = (min(i0 + kBX, a.nx) - i0) * (min(j0 + kBY, a.ny) - j0) * (min(k0 + kBZ, a.nz) - k0);
+            atomicAdd(&stats[1], cand * (unsigned long long)nvalid);
+        }
+    }
+    if (!valid) return;
+    // ---- epilogue: 66 moments -> 210 coefficients (times 1/sigma^2) ----
+    const int64_t node = ni + (int64_t)a.nx * (nj + (int64_t)a.ny * nk);
+    float outv[4];
+    int filled = 0;
+    for (int o = 0; o < a.stride; ++o) {
+        float val = 0.f;
+        if (o < 210 && ok) {
+            const int k = o / 21, e = o % 21;
+            const int r = sym_row(e), c = sym_col(e);
+            const int mx = kVp[k][0], my = kVp[k][1], mz = kVp[k][2];
+            if (r < 3 && c < 3) {
+                // (delta_rc - u_r u_c) / n^2
+                float v = -moment(hs, ls, tid, 2, mx + (r == 0) + (c == 0), my + (r == 1) + (c == 1),
+                                  mz + (r == 2) + (c == 2));
+                if (r == c) v += moment(hs, ls, tid, 2, mx, my, mz);
+                val = v;
+            } else if (r < 3) {
+                // (-[u]x)_{r b} / n = eps_{r b l} u_l / n
+                const int b = c - 3;
+                if (r != b) {
+                    const int l = 3 - r - b;
+                    const float sgn = ((r + 1) % 3 == b) ? 1.f : -1.f;  // eps_{r b l}
+                    val = sgn * moment(hs, ls, tid, 1, mx + (l == 0), my + (l == 1), mz + (l == 2));
+                }
+            } else {
+                const int ra = r - 3, cb = c - 3;
+                float v = -moment(hs, ls, tid, 0, mx + (ra == 0) + (cb == 0), my + (ra == 1) + (cb == 1),
+                                  mz + (ra == 2) + (cb == 2));
+                if (ra == cb) v += moment(hs, ls, tid, 0, mx, my, mz);
+                val = v;
+            }
+            val *= a.inv_sigma2;
+        }
+        if (a.storage == FIF_STORAGE_F32) {
+            outv[filled++] = val;
+            if (filled == 4) {
+                float4* dst = reinterpret_cast<float4*>(reinterpret_cast<float*>(a.out) + node * a.stride + (o - 3));
+                *dst = make_float4(outv[0], outv[1], outv[2], outv[3]);
+                filled = 0;
+            }
+        } else {
+            reinterpret_cast<__nv_bfloat16*>(a.out)[node * a.stride + o] = __float2bfloat16_rn(val);
+        }
+    }
+}
+
+}  // namespace
+
+BinGrid make_bin_grid(const fif_field* f) {
+    BinGrid bg;
+    const double rmax = f->params.r_max;
+    double size = f->params.bin_size > 0 ? f->params.bin_size : 1.0;
+    const double res = f->grid.res;
+    const int dims[3] = {f->grid.nx, f->grid.ny, f->grid.nz};
+    // rows of bins a brick can touch must fit the run table
+    const double ext = res * (std::max(kBY, kBZ) - 1) + 2.0 * (rmax + 0.02 + 1e-4 * rmax);
+    const double min_size = ext / (std::sqrt((double)kMaxRuns) - 2.0);
+    if (size < min_size) size = min_size;
+    bg.size = (float)size;
+    bg.inv_size = (float)(1.0 / size);
+    for (int a = 0; a < 3; ++a) {
+        const double lo = (double)f->grid.origin[a] - rmax - size;
+        const double hi = (double)f->grid.origin[a] + res * (dims[a] - 1) + rmax + size;
+        bg.lo[a] = (float)lo;
+        bg.n[a] = (int)std::ceil((hi - lo) / size) + 1;
+    }
+    return bg;
+}
+
+BuildLayout build_layout(const BinGrid& bg, int64_t n) {
+    BuildLayout L;
+    const int64_t nb = (int64_t)bg.n[0] * bg.n[1] * bg.n[2];
+    size_t off = 0;
+    L.sorted = off; off = align_up(off + sizeof(float4) * (size_t)std::max<int64_t>(n, 1), 256);
+    L.binof = off;  off = align_up(off + sizeof(int) * (size_t)std::max<int64_t>(n, 1), 256);
+    L.count = off;  off = align_up(off + sizeof(int) * (size_t)nb, 256);
+    L.start = off;  off = align_up(off + sizeof(int) * (size_t)(nb + 1), 256);
+    L.stats = off;  off = align_up(off + 4 * sizeof(unsigned long long), 256);
+    L.total = off;
+    return L;
+}
+
+int launch_build(const BuildArgs& a, cudaStream_t stream) {
+    const int64_t nb = (int64_t)a.bg.n[0] * a.bg.n[1] * a.bg.n[2];
+    if (nb > (int64_t)INT32_MAX - 1 || a.n > (int64_t)INT32_MAX) return FIF_ERANGE;
+    int* count = reinterpret_cast<int*>(a.ws + a.lay.count);
+    int* start = reinterpret_cast<int*>(a.ws + a.lay.start);
+    int* binof = reinterpret_cast<int*>(a.ws + a.lay.binof);
+    float4* sorted = reinterpret_cast<float4*>(a.ws + a.lay.sorted);
+    unsigned long long* stats = reinterpret_cast<unsigned long long*>(a.ws + a.lay.stats);
+    const int T = 256;
+    auto blocks = [&](int64_t work) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((work + T - 1) / T, 152 * 32)); };
+    fill_i32_kernel<<<blocks(nb), T, 0, stream>>>(count, nb, 0);
+    fill_i32_kernel<<<1, 32, 0, stream>>>(reinterpret_cast<int*>(stats), 8, 0);
+    if (a.n > 0) bin_count_kernel<<<blocks(a.n), T, 0, stream>>>(a.landmarks, a.n, a.bg, binof, count, stats);
+    bin_scan_kernel<<<1, 1024, 0, stream>>>(count, start, (int)nb);
+    if (a.n > 0) {
+        bin_scatter_kernel<<<blocks(a.n), T, 0, stream>>>(a.landmarks, a.n, binof, start, count, sorted);
+        bin_sort_kernel<<<blocks(nb), T, 0, stream>>>(sorted, start, (int)nb);
+    }
+    const int smem = (int)sizeof(BuildSmem);
+    if (cudaFuncSetAttribute(build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        return FIF_ECUDA;
+    const int64_t bricks = (int64_t)((a.nx + kBX - 1) / kBX) * ((a.ny + kBY - 1) / kBY) * ((a.nz + kBZ - 1) / kBZ);
+    if (bricks > (int64_t)INT32_MAX) return FIF_ERANGE;
+    build_kernel<<<(unsigned)bricks, kThreads, smem, stream>>>(a);
+    return cudaPeekAtLastError() == cudaSuccess ? FIF_OK : FIF_ECUDA;
+}
+
+}  // namespace fif

@@ -1,0 +1,358 @@
+// fif_abi.cu -- the extern "C" entry points declared in include/fif.h: argument checks,
+// launch configuration, field files and the device error word.  No device allocation.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "fif_internal.h"
+
+namespace {
+
+// first bounded-wait failure seen by any kernel on this device (per device copy)
+__device__ int g_device_error = 0;
+
+constexpr int32_t kVersion = 10000;  // 1.0.0
+constexpr int kMaxDevices = 64;
+int* g_err_ptr[kMaxDevices] = {nullptr};
+std::mutex g_err_mu;
+
+int* device_error_ptr() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    if (!g_err_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_device_error) != cudaSuccess) return nullptr;
+        g_err_ptr[dev] = static_cast<int*>(p);
+    }
+    return g_err_ptr[dev];
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+int stride_of(int32_t storage) {
+    return storage == FIF_STORAGE_F32 ? 216 : storage == FIF_STORAGE_BF16 ? 224 : 0;
+}
+size_t elem_of(int32_t storage) { return storage == FIF_STORAGE_F32 ? 4 : 2; }
+
+int check_grid(const fif_grid* g) {
+    if (!g) return FIF_EINVAL;
+    if (g->nx < 2 || g->ny < 2 || g->nz < 2) return FIF_EINVAL;
+    if (!(g->res > 0.f) || !std::isfinite(g->res)) return FIF_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(g->origin[a])) return FIF_EINVAL;
+    return FIF_OK;
+}
+
+int check_params(const fif_params* p) {
+    if (!p) return FIF_EINVAL;
+    if (!(p->half_fov > 0.0 && p->half_fov < M_PI)) return FIF_EINVAL;
+    if (!std::isfinite(p->v_alpha)) return FIF_EINVAL;
+    if (!(p->r_min >= 0.0) || !(p->r_max > p->r_min) || !std::isfinite(p->r_max)) return FIF_EINVAL;
+    if (!(p->sigma > 0.0) || !std::isfinite(p->sigma)) return FIF_EINVAL;
+    if (p->bin_size < 0.f || !std::isfinite(p->bin_size)) return FIF_EINVAL;
+    return FIF_OK;
+}
+
+int check_field(const fif_field* f) {
+    if (!f) return FIF_EINVAL;
+    int rc = check_grid(&f->grid);
+    if (rc) return rc;
+    if ((rc = check_params(&f->params))) return rc;
+    if (stride_of(f->storage) == 0 || f->stride != stride_of(f->storage)) return FIF_EINVAL;
+    if (!f->coeffs) return FIF_EINVAL;
+    if (!aligned16(f->coeffs)) return FIF_EALIGN;
+    if (f->bytes < fif_field_bytes(&f->grid, f->storage)) return FIF_ESIZE;
+    return FIF_OK;
+}
+
+// (k0, k1, k2) from v(0) = 1, v(pi) = 0, v(alpha) = v_alpha (Eq. quadratic_conditions):
+// the first two give k1 = 1/2 and k0 + k2 = 1/2; the third then fixes k2.
+void quad_coeffs(double alpha, double va, double k[3]) {
+    const double c = std::cos(alpha);
+    const double k2 = (va - 0.5 - 0.5 * c) / (c * c - 1.0);
+    k[0] = 0.5 - k2;
+    k[1] = 0.5;
+    k[2] = k2;
+}
+
+fif::QueryArgs query_args(const fif_field* f, const float* poses, int64_t m, int32_t flags) {
+    fif::QueryArgs a{};
+    a.coeffs = f->coeffs;
+    a.storage = f->storage;
+    a.stride = f->stride;
+    a.ox = f->grid.origin[0]; a.oy = f->grid.origin[1]; a.oz = f->grid.origin[2];
+    a.res = f->grid.res;
+    a.nx = f->grid.nx; a.ny = f->grid.ny; a.nz = f->grid.nz;
+    a.k0 = (float)f->k[0]; a.k1 = (float)f->k[1]; a.k2 = (float)f->k[2];
+    a.poses = poses;
+    a.m = m;
+    a.flags = flags;
+    a.err = device_error_ptr();
+    return a;
+}
+
+uint64_t fnv1a(const unsigned char* p, size_t n, uint64_t h = 1469598103934665603ull) {
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+struct FileHeader {
+    char magic[8];        // "FIFFIELD"
+    int32_t version;
+    int32_t storage;
+    int32_t stride;
+    int32_t pad;
+    fif_grid grid;
+    fif_params params;
+    uint64_t payload_bytes;
+    uint64_t checksum;
+};
+
+}  // namespace
+
+extern "C" {
+
+int32_t fif_version(void) { return kVersion; }
+
+const char* fif_status_str(int32_t code) {
+    switch (code) {
+        case FIF_OK: return "ok";
+        case FIF_EINVAL: return "invalid argument";
+        case FIF_ESIZE: return "buffer too small";
+        case FIF_EALIGN: return "device pointer not 16-byte aligned";
+        case FIF_ECUDA: return "CUDA error";
+        case FIF_ETIMEOUT: return "bounded device wait ran out";
+        case FIF_EIO: return "file I/O error";
+        case FIF_EFORMAT: return "file format mismatch";
+        case FIF_ERANGE: return "size exceeds a fixed maximum";
+        default: return "unknown status";
+    }
+}
+
+size_t fif_field_bytes(const fif_grid* grid, int32_t storage) {
+    if (check_grid(grid) || stride_of(storage) == 0) return 0;
+    const size_t nodes = (size_t)grid->nx * grid->ny * grid->nz;
+    return nodes * stride_of(storage) * elem_of(storage);
+}
+
+int32_t fif_field_init(fif_field* field, const fif_grid* grid, const fif_params* params, int32_t storage,
+                       void* d_coeffs, size_t bytes) {
+    if (!field) return FIF_EINVAL;
+    int rc = check_grid(grid);
+    if (rc) return rc;
+    if ((rc = check_params(params))) return rc;
+    if (stride_of(storage) == 0) return FIF_EINVAL;
+    if (!d_coeffs) return FIF_EINVAL;
+    if (!aligned16(d_coeffs)) return FIF_EALIGN;
+    if (bytes < fif_field_bytes(grid, storage)) return FIF_ESIZE;
+    std::memset(field, 0, sizeof(*field));
+    field->grid = *grid;
+    field->params = *params;
+    field->storage = storage;
+    field->stride = stride_of(storage);
+    field->coeffs = d_coeffs;
+    field->bytes = bytes;
+    quad_coeffs(params->half_fov, params->v_alpha, field->k);
+    return FIF_OK;
+}
+
+size_t fif_build_workspace_bytes(const fif_field* field, int64_t n) {
+    if (check_field(field) || n < 0) return 0;
+    const fif::BinGrid bg = fif::make_bin_grid(field);
+    return fif::build_layout(bg, n).total;
+}
+
+int32_t fif_build(fif_field* field, const float* d_landmarks, int64_t n, void* d_ws, size_t ws_bytes,
+                  fif_stream_t stream) {
+    int rc = check_field(field);
+    if (rc) return rc;
+    if (n < 0 || (n > 0 && !d_landmarks) || !d_ws) return FIF_EINVAL;
+    if (!aligned16(d_ws) || (n > 0 && (reinterpret_cast<uintptr_t>(d_landmarks) & 3u))) return FIF_EALIGN;
+    const fif::BinGrid bg = fif::make_bin_grid(field);
+    const fif::BuildLayout lay = fif::build_layout(bg, n);
+    if (ws_bytes < lay.total) return FIF_ESIZE;
+    fif::BuildArgs a{};
+    a.landmarks = d_landmarks;
+    a.n = n;
+    a.ws = static_cast<unsigned char*>(d_ws);
+    a.lay = lay;
+    a.bg = bg;
+    a.ox = field->grid.origin[0]; a.oy = field->grid.origin[1]; a.oz = field->grid.origin[2];
+    a.res = field->grid.res;
+    a.nx = field->grid.nx; a.ny = field->grid.ny; a.nz = field->grid.nz;
+    a.rmin2 = (float)(field->params.r_min * field->params.r_min);
+    a.rmax2 = (float)(field->params.r_max * field->params.r_max);
+    a.rcull = (float)(field->params.r_max + 0.01 + 1e-4 * field->params.r_max);
+    a.inv_sigma2 = (float)(1.0 / (field->params.sigma * field->params.sigma));
+    a.storage = field->storage;
+    a.stride = field->stride;
+    a.out = field->coeffs;
+    a.err = device_error_ptr();
+    return fif::launch_build(a, stream);
+}
+
+int32_t fif_query(const fif_field* field, const float* d_poses, int64_t m, int32_t flags, float* d_fim,
+                  double* d_metrics, int8_t* d_sign, int32_t* d_status, fif_stream_t stream) {
+    int rc = check_field(field);
+    if (rc) return rc;
+    if (m < 0 || (m > 0 && !d_poses)) return FIF_EINVAL;
+    if (flags & ~(FIF_Q_NEAREST | FIF_Q_WORLD | FIF_Q_METRICS)) return FIF_EINVAL;
+    if ((flags & FIF_Q_METRICS) && !d_metrics && !d_sign && !d_status) return FIF_EINVAL;
+    if (field->storage != FIF_STORAGE_F32) return FIF_EINVAL;
+    if (m == 0) return FIF_OK;
+    if (reinterpret_cast<uintptr_t>(d_poses) & 3u) return FIF_EALIGN;
+    fif::QueryArgs a = query_args(field, d_poses, m, flags);
+    a.fim = d_fim;
+    a.metrics = d_metrics;
+    a.sign = d_sign;
+    a.status = d_status;
+    return fif::launch_query(a, stream);
+}
+
+int32_t fif_query_backward(const fif_field* field, const float* d_poses, int64_t m, int32_t flags,
+                           const float* d_fim, const double* d_grad_metrics, float* d_grad_pose,
+                           fif_stream_t stream) {
+    int rc = check_field(field);
+    if (rc) return rc;
+    if (m < 0 || (m > 0 && (!d_poses || !d_fim || !d_grad_metrics || !d_grad_pose))) return FIF_EINVAL;
+    if (flags & ~(FIF_Q_WORLD | FIF_Q_METRICS)) return FIF_EINVAL;  // trilinear only
+    if (field->storage != FIF_STORAGE_F32) return FIF_EINVAL;
+    if (m == 0) return FIF_OK;
+    fif::QueryArgs q = query_args(field, d_poses, m, flags);
+    fif::AdjointArgs a{};
+    a.coeffs = q.coeffs; a.storage = q.storage; a.stride = q.stride;
+    a.ox = q.ox; a.oy = q.oy; a.oz = q.oz; a.res = q.res;
+    a.nx = q.nx; a.ny = q.ny; a.nz = q.nz;
+    a.k0 = q.k0; a.k1 = q.k1; a.k2 = q.k2;
+    a.poses = d_poses;
+    a.m = m;
+    a.flags = flags;
+    a.fim = d_fim;
+    a.gm = d_grad_metrics;
+    a.grad = d_grad_pose;
+    a.err = q.err;
+    return fif::launch_adjoint(a, stream);
+}
+
+int32_t fif_pointcloud_fim(const float* d_landmarks, int64_t n, const fif_params* params, const fif_pinhole* cam,
+                           const float* d_poses, int64_t m, int32_t flags, float* d_fim, double* d_metrics,
+                           int8_t* d_sign, int32_t* d_status, fif_stream_t stream) {
+    int rc = check_params(params);
+    if (rc) return rc;
+    if (!cam || cam->width <= 0 || cam->height <= 0) return FIF_EINVAL;
+    if (n < 0 || m < 0 || (n > 0 && !d_landmarks) || (m > 0 && !d_poses)) return FIF_EINVAL;
+    if (flags & ~(FIF_Q_WORLD | FIF_Q_METRICS)) return FIF_EINVAL;
+    if (m == 0) return FIF_OK;
+    fif::PointCloudArgs a{};
+    a.landmarks = d_landmarks;
+    a.n = n;
+    a.rmin2 = (float)(params->r_min * params->r_min);
+    a.rmax2 = (float)(params->r_max * params->r_max);
+    a.inv_sigma2 = (float)(1.0 / (params->sigma * params->sigma));
+    a.fx = cam->fx; a.fy = cam->fy; a.cx = cam->cx; a.cy = cam->cy;
+    a.W = (float)cam->width; a.H = (float)cam->height;
+    a.poses = d_poses;
+    a.m = m;
+    a.flags = flags;
+    a.fim = d_fim;
+    a.metrics = d_metrics;
+    a.sign = d_sign;
+    a.status = d_status;
+    return fif::launch_pointcloud(a, stream);
+}
+
+int32_t fif_field_save(const fif_field* field, const char* path, void* host_staging, fif_stream_t stream) {
+    int rc = check_field(field);
+    if (rc) return rc;
+    if (!path) return FIF_EINVAL;
+    const size_t bytes = fif_field_bytes(&field->grid, field->storage);
+    unsigned char* buf = static_cast<unsigned char*>(host_staging);
+    unsigned char* own = nullptr;
+    if (!buf) {
+        own = static_cast<unsigned char*>(std::malloc(bytes));
+        if (!own) return FIF_ESIZE;
+        buf = own;
+    }
+    int result = FIF_OK;
+    if (cudaMemcpyAsync(buf, field->coeffs, bytes, cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess) {
+        result = FIF_ECUDA;
+    } else {
+        FileHeader h{};
+        std::memcpy(h.magic, "FIFFIELD", 8);
+        h.version = kVersion;
+        h.storage = field->storage;
+        h.stride = field->stride;
+        h.grid = field->grid;
+        h.params = field->params;
+        h.payload_bytes = bytes;
+        h.checksum = fnv1a(buf, bytes);
+        FILE* fp = std::fopen(path, "wb");
+        if (!fp) {
+            result = FIF_EIO;
+        } else {
+            if (std::fwrite(&h, sizeof(h), 1, fp) != 1 || std::fwrite(buf, 1, bytes, fp) != bytes) result = FIF_EIO;
+            if (std::fclose(fp) != 0) result = FIF_EIO;
+        }
+    }
+    std::free(own);
+    return result;
+}
+
+int32_t fif_field_load(fif_field* field, const char* path, void* d_coeffs, size_t bytes, void* host_staging,
+                       fif_stream_t stream) {
+    if (!field || !path || !d_coeffs) return FIF_EINVAL;
+    FILE* fp = std::fopen(path, "rb");
+    if (!fp) return FIF_EIO;
+    FileHeader h{};
+    if (std::fread(&h, sizeof(h), 1, fp) != 1) { std::fclose(fp); return FIF_EFORMAT; }
+    if (std::memcmp(h.magic, "FIFFIELD", 8) != 0 || h.version != kVersion || stride_of(h.storage) == 0 ||
+        h.stride != stride_of(h.storage) || check_grid(&h.grid) || check_params(&h.params) ||
+        h.payload_bytes != fif_field_bytes(&h.grid, h.storage)) {
+        std::fclose(fp);
+        return FIF_EFORMAT;
+    }
+    if (bytes < h.payload_bytes) { std::fclose(fp); return FIF_ESIZE; }
+    unsigned char* buf = static_cast<unsigned char*>(host_staging);
+    unsigned char* own = nullptr;
+    if (!buf) {
+        own = static_cast<unsigned char*>(std::malloc(h.payload_bytes));
+        if (!own) { std::fclose(fp); return FIF_ESIZE; }
+        buf = own;
+    }
+    int result = FIF_OK;
+    if (std::fread(buf, 1, h.payload_bytes, fp) != h.payload_bytes) result = FIF_EFORMAT;
+    std::fclose(fp);
+    if (result == FIF_OK && fnv1a(buf, h.payload_bytes) != h.checksum) result = FIF_EFORMAT;
+    if (result == FIF_OK) {
+        result = fif_field_init(field, &h.grid, &h.params, h.storage, d_coeffs, bytes);
+        if (result == FIF_OK &&
+            (cudaMemcpyAsync(d_coeffs, buf, h.payload_bytes, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+             cudaStreamSynchronize(stream) != cudaSuccess))
+            result = FIF_ECUDA;
+    }
+    std::free(own);
+    return result;
+}
+
+int32_t fif_device_error(int32_t* out_code, int32_t reset, fif_stream_t stream) {
+    if (!out_code) return FIF_EINVAL;
+    int* p = device_error_ptr();
+    if (!p) return FIF_ECUDA;
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return FIF_ECUDA;
+    int v = 0;
+    if (cudaMemcpy(&v, p, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return FIF_ECUDA;
+    if (reset) {
+        const int z = 0;
+        if (cudaMemcpy(p, &z, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) return FIF_ECUDA;
+    }
+    *out_code = v;
+    return FIF_OK;
+}
+
+}  // extern "C"

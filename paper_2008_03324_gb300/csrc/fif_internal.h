@@ -1,0 +1,106 @@
+// fif_internal.h -- launch interfaces between the C ABI (fif_abi.cu) and the kernel files.
+#pragma once
+
+#include <algorithm>
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/fif.h"
+
+namespace fif {
+
+// ---- query ---------------------------------------------------------------------------
+struct QueryArgs {
+    const void* coeffs;
+    int storage;
+    int stride;
+    float ox, oy, oz, res;
+    int nx, ny, nz;
+    float k0, k1, k2;
+    const float* poses;
+    int64_t m;
+    int flags;
+    float* fim;
+    double* metrics;
+    int8_t* sign;
+    int32_t* status;
+    int* err;
+};
+int launch_query(const QueryArgs& a, cudaStream_t stream);
+
+// ---- query adjoint -------------------------------------------------------------------
+struct AdjointArgs {
+    const void* coeffs;
+    int storage;
+    int stride;
+    float ox, oy, oz, res;
+    int nx, ny, nz;
+    float k0, k1, k2;
+    const float* poses;
+    int64_t m;
+    int flags;
+    const float* fim;
+    const double* gm;
+    float* grad;
+    int* err;
+};
+int launch_adjoint(const AdjointArgs& a, cudaStream_t stream);
+
+// ---- build ---------------------------------------------------------------------------
+struct BinGrid {
+    float lo[3];     // corner of bin (0,0,0)
+    float size;      // bin edge
+    float inv_size;
+    int n[3];        // bins per axis
+};
+
+struct BuildLayout {
+    size_t sorted;   // float4[n]  (x, y, z, index bits)
+    size_t binof;    // int32[n]
+    size_t count;    // int32[nbins]  (count, then cursor)
+    size_t start;    // int32[nbins + 1]
+    size_t stats;    // uint64[4]  (in-shell pairs, candidate pairs, dropped landmarks, -)
+    size_t total;
+};
+
+BinGrid make_bin_grid(const fif_field* f);
+BuildLayout build_layout(const BinGrid& bg, int64_t n);
+
+struct BuildArgs {
+    const float* landmarks;
+    int64_t n;
+    unsigned char* ws;
+    BuildLayout lay;
+    BinGrid bg;
+    float ox, oy, oz, res;
+    int nx, ny, nz;
+    float rmin2, rmax2, rcull;
+    float inv_sigma2;
+    int storage;
+    int stride;
+    void* out;
+    int* err;
+};
+int launch_build(const BuildArgs& a, cudaStream_t stream);
+
+// ---- point cloud ---------------------------------------------------------------------
+struct PointCloudArgs {
+    const float* landmarks;
+    int64_t n;
+    float rmin2, rmax2;
+    float inv_sigma2;
+    float fx, fy, cx, cy, W, H;
+    const float* poses;
+    int64_t m;
+    int flags;
+    float* fim;
+    double* metrics;
+    int8_t* sign;
+    int32_t* status;
+};
+int launch_pointcloud(const PointCloudArgs& a, cudaStream_t stream);
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace fif

@@ -1,0 +1,276 @@
+"""ctypes binding of libfif.so (the C ABI in include/fif.h) -- argument marshalling only.
+
+Every function here passes raw device pointers, sizes and the current CUDA stream to the
+library; all arithmetic runs in the library's kernels.  There is no CPU fallback: if the
+library is missing, :func:`lib` raises.
+
+The same names as the C ABI: :func:`field_bytes`, :func:`field_init`,
+:func:`build_workspace_bytes`, :func:`build`, :func:`query`, :func:`query_backward`,
+:func:`pointcloud_fim`, :func:`field_save`, :func:`field_load`, :func:`device_error`.
+:class:`Field` bundles a field with its torch-owned storage, and :class:`FifQuery` is the
+autograd function whose backward is the library's hand-written adjoint.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfif.so")
+
+# ---- constants (mirror include/fif.h) -------------------------------------------------
+OK, EINVAL, ESIZE, EALIGN, ECUDA, ETIMEOUT, EIO, EFORMAT, ERANGE = 0, -1, -2, -3, -4, -5, -6, -7, -8
+POSE_OUTSIDE, POSE_QUAT, POSE_NOT_PD, POSE_NAN = 1, 2, 4, 8
+STORAGE_F32, STORAGE_BF16 = 0, 1
+Q_TRILINEAR, Q_NEAREST, Q_CAMERA, Q_WORLD = 0x0, 0x1, 0x0, 0x2
+Q_TRACE, Q_LOGDET, Q_LMIN, Q_METRICS = 0x10, 0x20, 0x40, 0x70
+STRIDE = {STORAGE_F32: 216, STORAGE_BF16: 224}
+
+
+class FifError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__(f"{what}: {status_str(code)} ({code})")
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("origin", ctypes.c_float * 3), ("res", ctypes.c_float),
+                ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("half_fov", ctypes.c_double), ("v_alpha", ctypes.c_double), ("r_min", ctypes.c_double),
+                ("r_max", ctypes.c_double), ("sigma", ctypes.c_double), ("bin_size", ctypes.c_float),
+                ("reserved", ctypes.c_int32)]
+
+
+class Pinhole(ctypes.Structure):
+    _fields_ = [("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32)]
+
+
+class FieldC(ctypes.Structure):
+    _fields_ = [("grid", Grid), ("params", Params), ("storage", ctypes.c_int32), ("stride", ctypes.c_int32),
+                ("coeffs", ctypes.c_void_p), ("bytes", ctypes.c_size_t), ("k", ctypes.c_double * 3)]
+
+
+_lib = None
+_lock = threading.Lock()
+_VP = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+
+_SIGS = {
+    "fif_version": (_I32, []),
+    "fif_status_str": (ctypes.c_char_p, [_I32]),
+    "fif_field_bytes": (ctypes.c_size_t, [ctypes.POINTER(Grid), _I32]),
+    "fif_field_init": (_I32, [ctypes.POINTER(FieldC), ctypes.POINTER(Grid), ctypes.POINTER(Params), _I32, _VP,
+                              ctypes.c_size_t]),
+    "fif_build_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(FieldC), _I64]),
+    "fif_build": (_I32, [ctypes.POINTER(FieldC), _VP, _I64, _VP, ctypes.c_size_t, _VP]),
+    "fif_query": (_I32, [ctypes.POINTER(FieldC), _VP, _I64, _I32, _VP, _VP, _VP, _VP, _VP]),
+    "fif_query_backward": (_I32, [ctypes.POINTER(FieldC), _VP, _I64, _I32, _VP, _VP, _VP, _VP]),
+    "fif_pointcloud_fim": (_I32, [_VP, _I64, ctypes.POINTER(Params), ctypes.POINTER(Pinhole), _VP, _I64, _I32,
+                                  _VP, _VP, _VP, _VP, _VP]),
+    "fif_field_save": (_I32, [ctypes.POINTER(FieldC), ctypes.c_char_p, _VP, _VP]),
+    "fif_field_load": (_I32, [ctypes.POINTER(FieldC), ctypes.c_char_p, _VP, ctypes.c_size_t, _VP, _VP]),
+    "fif_device_error": (_I32, [ctypes.POINTER(_I32), _I32, _VP]),
+}
+SYMBOLS = tuple(_SIGS)
+
+
+def lib(path: str = LIB_PATH):
+    """Load libfif.so (raises if it has not been built -- there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError(f"{path} is missing: build it with `python -m paper_2008_03324_gb300.build`")
+            L = ctypes.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def status_str(code: int) -> str:
+    try:
+        return lib().fif_status_str(int(code)).decode()
+    except Exception:  # library not loadable
+        return "unknown"
+
+
+def _check(rc, what):
+    if rc != OK:
+        raise FifError(rc, what)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def make_grid(origin, res, dims) -> Grid:
+    g = Grid()
+    for a in range(3):
+        g.origin[a] = float(origin[a])
+    g.res = float(res)
+    g.nx, g.ny, g.nz = (int(d) for d in dims)
+    return g
+
+
+def make_params(half_fov=math.pi / 4, v_alpha=0.5, r_min=0.1, r_max=8.0, sigma=1.0, bin_size=0.0) -> Params:
+    p = Params()
+    p.half_fov, p.v_alpha, p.r_min, p.r_max, p.sigma = half_fov, v_alpha, r_min, r_max, sigma
+    p.bin_size = bin_size
+    return p
+
+
+def make_pinhole(fx=320.0, fy=320.0, cx=320.0, cy=320.0, width=640, height=640) -> Pinhole:
+    c = Pinhole()
+    c.fx, c.fy, c.cx, c.cy, c.width, c.height = fx, fy, cx, cy, int(width), int(height)
+    return c
+
+
+def field_bytes(grid: Grid, storage=STORAGE_F32) -> int:
+    return int(lib().fif_field_bytes(ctypes.byref(grid), int(storage)))
+
+
+def field_init(grid: Grid, params: Params, storage, coeffs: torch.Tensor) -> FieldC:
+    f = FieldC()
+    _check(lib().fif_field_init(ctypes.byref(f), ctypes.byref(grid), ctypes.byref(params), int(storage),
+                                _ptr(coeffs), coeffs.numel() * coeffs.element_size()), "fif_field_init")
+    return f
+
+
+def build_workspace_bytes(field: FieldC, n: int) -> int:
+    return int(lib().fif_build_workspace_bytes(ctypes.byref(field), int(n)))
+
+
+def build(field: FieldC, landmarks: torch.Tensor, workspace: torch.Tensor, stream=None):
+    assert landmarks.is_cuda and landmarks.dtype == torch.float32 and landmarks.is_contiguous()
+    _check(lib().fif_build(ctypes.byref(field), _ptr(landmarks), landmarks.shape[0], _ptr(workspace),
+                           workspace.numel() * workspace.element_size(), _stream(stream)), "fif_build")
+
+
+def query(field: FieldC, poses: torch.Tensor, flags=Q_METRICS, fim=None, metrics=None, sign=None, status=None,
+          stream=None):
+    assert poses.is_cuda and poses.dtype == torch.float32 and poses.is_contiguous()
+    _check(lib().fif_query(ctypes.byref(field), _ptr(poses), poses.shape[0], int(flags), _ptr(fim), _ptr(metrics),
+                           _ptr(sign), _ptr(status), _stream(stream)), "fif_query")
+
+
+def query_backward(field: FieldC, poses, fim, grad_metrics, grad_pose, flags=Q_METRICS, stream=None):
+    _check(lib().fif_query_backward(ctypes.byref(field), _ptr(poses), poses.shape[0], int(flags), _ptr(fim),
+                                    _ptr(grad_metrics), _ptr(grad_pose), _stream(stream)), "fif_query_backward")
+
+
+def pointcloud_fim(landmarks, params: Params, camera: Pinhole, poses, flags=Q_METRICS, fim=None, metrics=None,
+                   sign=None, status=None, stream=None):
+    _check(lib().fif_pointcloud_fim(_ptr(landmarks), landmarks.shape[0], ctypes.byref(params), ctypes.byref(camera),
+                                    _ptr(poses), poses.shape[0], int(flags), _ptr(fim), _ptr(metrics), _ptr(sign),
+                                    _ptr(status), _stream(stream)), "fif_pointcloud_fim")
+
+
+def field_save(field: FieldC, path: str, stream=None):
+    _check(lib().fif_field_save(ctypes.byref(field), path.encode(), None, _stream(stream)), "fif_field_save")
+
+
+def field_load(path: str, coeffs: torch.Tensor, stream=None) -> FieldC:
+    f = FieldC()
+    _check(lib().fif_field_load(ctypes.byref(f), path.encode(), _ptr(coeffs), coeffs.numel() * coeffs.element_size(),
+                                None, _stream(stream)), "fif_field_load")
+    return f
+
+
+def device_error(reset=True, stream=None) -> int:
+    v = _I32(0)
+    _check(lib().fif_device_error(ctypes.byref(v), int(bool(reset)), _stream(stream)), "fif_device_error")
+    return int(v.value)
+
+
+# ---------------------------------------------------------------------------
+# convenience objects
+# ---------------------------------------------------------------------------
+
+class Field:
+    """A field with torch-owned device storage."""
+
+    def __init__(self, origin, res, dims, params: Params | None = None, storage=STORAGE_F32, device="cuda"):
+        self.grid = make_grid(origin, res, dims)
+        self.params = params if params is not None else make_params()
+        nbytes = field_bytes(self.grid, storage)
+        if nbytes == 0:
+            raise FifError(EINVAL, "fif_field_bytes")
+        dt = torch.float32 if storage == STORAGE_F32 else torch.bfloat16
+        n_nodes = int(dims[0]) * int(dims[1]) * int(dims[2])
+        self.storage = storage
+        self.coeffs = torch.zeros(n_nodes, STRIDE[storage], dtype=dt, device=device)
+        self.c = field_init(self.grid, self.params, storage, self.coeffs)
+        self.dims = tuple(int(d) for d in dims)
+
+    @property
+    def n_nodes(self):
+        return self.coeffs.shape[0]
+
+    def build(self, landmarks: torch.Tensor, workspace: torch.Tensor | None = None, stream=None):
+        need = build_workspace_bytes(self.c, landmarks.shape[0])
+        if workspace is None or workspace.numel() * workspace.element_size() < need:
+            workspace = torch.empty(need, dtype=torch.uint8, device=self.coeffs.device)
+        build(self.c, landmarks, workspace, stream)
+        return workspace
+
+    def query(self, poses, flags=Q_METRICS, want_fim=True, stream=None):
+        m = poses.shape[0]
+        dev = poses.device
+        fim = torch.empty(m, 21, dtype=torch.float32, device=dev) if want_fim else None
+        met = torch.empty(m, 3, dtype=torch.float64, device=dev)
+        sg = torch.empty(m, dtype=torch.int8, device=dev)
+        st = torch.empty(m, dtype=torch.int32, device=dev)
+        query(self.c, poses, flags, fim, met, sg, st, stream)
+        return fim, met, sg, st
+
+
+def build_stats(workspace: torch.Tensor, field: Field, n_landmarks: int):
+    """(in-shell pairs, candidate pairs, dropped landmarks) counted by the last build (reads
+    the statistics block at the end of the workspace)."""
+    need = build_workspace_bytes(field.c, n_landmarks)
+    # the statistics block is the last 256-byte-aligned block of the layout
+    raw = workspace[need - 256: need - 256 + 32].view(torch.int64).cpu()
+    return int(raw[0]), int(raw[1]), int(raw[2])
+
+
+class FifQuery(torch.autograd.Function):
+    """metrics = FifQuery.apply(t, phi, quat, field, flags) -> [m, 3] (trace, log|det|, lambda_min).
+
+    The pose is (t, R(quat) exp(phi^)) evaluated at phi = 0: `phi` must be a zero [m, 3] tensor
+    that only routes the gradient of the right (camera-frame) so(3) perturbation.  Backward
+    runs the library's adjoint kernel and returns d/dt [m, 3] and d/dphi [m, 3]."""
+
+    @staticmethod
+    def forward(ctx, t, phi, quat, field: Field, flags=Q_METRICS):
+        poses = torch.cat([t.detach(), quat.detach()], dim=1).to(torch.float32).contiguous()
+        fim, met, sg, st = field.query(poses, flags)
+        ctx.field = field
+        ctx.flags = flags
+        ctx.save_for_backward(poses, fim)
+        ctx.mark_non_differentiable(sg, st)
+        return met, sg, st
+
+    @staticmethod
+    def backward(ctx, g_met, g_sg=None, g_st=None):
+        poses, fim = ctx.saved_tensors
+        g = g_met.detach().to(torch.float64).contiguous()
+        out = torch.empty(poses.shape[0], 6, dtype=torch.float32, device=poses.device)
+        query_backward(ctx.field.c, poses, fim, g, out, ctx.flags & (Q_WORLD | Q_METRICS))
+        return out[:, :3], out[:, 3:], None, None, None

@@ -1,0 +1,99 @@
+"""Shared test fixtures: the seeded workloads, oracle results cached per process, and the
+packing of an oracle-built field into the library's documented storage layout."""
+import functools
+import math
+
+import numpy as np
+
+import oracle as O
+from paper_2008_03324_gb300 import synth
+
+TAU_F32 = 1e-5    # relative Frobenius bound for single-precision storage
+TAU_BF16 = 1e-2   # relative Frobenius bound for bfloat16 storage
+
+# sym packing order of the library (21 upper-triangular entries, row-major)
+SYM_RC = [(r, c) for r in range(6) for c in range(r, 6)]
+SYM_R = np.array([rc[0] for rc in SYM_RC])
+SYM_C = np.array([rc[1] for rc in SYM_RC])
+SYM_W = np.where(SYM_R == SYM_C, 1.0, 2.0)   # weight of an entry in the full Frobenius sum
+
+
+def unpack21(x):
+    """[..., 21] -> [..., 6, 6] symmetric."""
+    x = np.asarray(x, dtype=np.float64)
+    out = np.zeros(x.shape[:-1] + (6, 6))
+    out[..., SYM_R, SYM_C] = x
+    out[..., SYM_C, SYM_R] = x
+    return out
+
+
+def pack21(M):
+    M = np.asarray(M)
+    return M[..., SYM_R, SYM_C]
+
+
+def fro(M):
+    M = np.asarray(M, dtype=np.float64)
+    return np.sqrt((M ** 2).sum(axis=(-2, -1)))
+
+
+def rel_fro(A, B):
+    """||A - B||_F / ||B||_F per matrix (full symmetric 6x6)."""
+    return fro(np.asarray(A) - np.asarray(B)) / np.maximum(fro(B), 1e-300)
+
+
+def pack_field(F_local, stride=216):
+    """Oracle node-local coefficients [N, 10, 6, 6] -> library layout [N, stride] float32."""
+    N = F_local.shape[0]
+    out = np.zeros((N, stride), np.float32)
+    out[:, :210] = F_local[:, :, SYM_R, SYM_C].reshape(N, 210).astype(np.float32)
+    return out
+
+
+def unpack_field(buf):
+    """Library layout [N, stride] -> [N, 10, 6, 6] float64."""
+    buf = np.asarray(buf, dtype=np.float64)
+    return unpack21(buf[:, :210].reshape(-1, 10, 21))
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+
+ROOM = dict(seed=1, n=2000, grid=synth.ROOM_GRID, r_max=8.0, pose_seed=2, m=1000)
+WAREHOUSE = dict(seed=2, n=200_000, grid=synth.WAREHOUSE_GRID, r_max=10.0)
+
+
+@functools.lru_cache(maxsize=None)
+def room_scene():
+    return synth.room_landmarks(seed=ROOM["seed"], n=ROOM["n"])
+
+
+@functools.lru_cache(maxsize=None)
+def room_poses(m=1000):
+    return synth.random_poses(ROOM["pose_seed"], m, (0, 0, 0), (10, 10, 3))
+
+
+def oracle_grid(spec):
+    return O.make_grid(spec.origin, spec.res, spec.dims)
+
+
+@functools.lru_cache(maxsize=None)
+def room_field_oracle(about_node: bool):
+    sc = room_scene()
+    return O.full_field(sc.landmarks, oracle_grid(ROOM["grid"]), O.make_params(r_max=ROOM["r_max"]),
+                        about_node=about_node)
+
+
+@functools.lru_cache(maxsize=None)
+def warehouse_scene():
+    return synth.warehouse(seed=WAREHOUSE["seed"], n=WAREHOUSE["n"])
+
+
+def metric_tolerances(I_ref, tau):
+    """Per-matrix bounds on the metric errors implied by ||dI||_F <= tau ||I||_F:
+    |d trace| <= sqrt(6) tau ||I||, |d lambda_min| <= tau ||I||, |d log|det|| <= tau ||I|| ||I^-1||
+    (first order, doubled)."""
+    n = fro(I_ref)
+    inv = np.array([fro(np.linalg.pinv(M)) for M in I_ref])
+    return math.sqrt(6) * tau * n, tau * n, 2.0 * tau * n * inv

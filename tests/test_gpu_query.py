@@ -1,0 +1,135 @@
+"""GPU query (fif_query) against the FP64 oracle, element by element on the same seeded
+inputs: the 10 x 10 x 3 m room (21 x 21 x 7 nodes at 0.5 m, 2000 landmarks, 1000 poses --
+a ragged tail of 8 past 31 full groups of 32), plus edge cases."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2008_03324_gb300 import synth
+from tests import _fixtures as X
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    from paper_2008_03324_gb300 import build as B
+    B.build()
+    from paper_2008_03324_gb300 import fif
+    return fif
+
+
+def uploaded_room_field(F, v_alpha=0.5, storage=0):
+    spec = X.ROOM["grid"]
+    field = F.Field(spec.origin, spec.res, spec.dims, F.make_params(r_max=X.ROOM["r_max"], v_alpha=v_alpha),
+                    storage=storage)
+    buf = X.pack_field(X.room_field_oracle(True))
+    field.coeffs.copy_(torch.from_numpy(buf).to(field.coeffs.dtype))
+    return field
+
+
+def oracle_query(poses, v_alpha=0.5, frame=O.FRAME_CAMERA, interp=O.INTERP_TRILINEAR):
+    grid = X.oracle_grid(X.ROOM["grid"])
+    nodes, w, dw, st = O.query_cells(grid, poses, interp)
+    k = O.quad_coeffs(math.pi / 4, v_alpha)
+    I = O.query(X.room_field_oracle(False)[nodes], w, poses, k, frame)
+    return I, st
+
+
+def run(F, field, poses, flags=None):
+    p = torch.from_numpy(np.ascontiguousarray(poses, np.float32)).cuda()
+    fim, met, sg, st = field.query(p, F.Q_METRICS if flags is None else flags)
+    torch.cuda.synchronize()
+    return fim.cpu().numpy(), met.cpu().numpy(), sg.cpu().numpy(), st.cpu().numpy()
+
+
+def check_metrics(I_ref, met, sg, tau, check_sign=True):
+    mo = O.metrics(I_ref)
+    t_tr, t_lm, t_ld = X.metric_tolerances(I_ref, tau)
+    assert np.all(np.abs(met[:, 0] - mo[:, 0]) <= t_tr)
+    assert np.all(np.abs(met[:, 2] - mo[:, 3]) <= t_lm)
+    ok = t_ld < 1.0   # log|det| is meaningful where the FIM is not near-singular
+    assert np.all(np.abs(met[ok, 1] - mo[ok, 1]) <= t_ld[ok])
+    if check_sign:
+        np.testing.assert_array_equal(sg[ok], mo[ok, 2].astype(np.int8))
+
+
+@pytest.mark.parametrize("v_alpha", [0.5, 0.8])
+def test_room_query_matches_oracle(F, v_alpha):
+    field = uploaded_room_field(F, v_alpha)
+    poses = X.room_poses(1000)
+    fim, met, sg, st = run(F, field, poses)
+    I_ref, st_ref = oracle_query(poses, v_alpha)
+    err = X.rel_fro(X.unpack21(fim), I_ref)
+    assert err.max() <= X.TAU_F32, err.max()
+    check_metrics(I_ref, met, sg, X.TAU_F32)
+    np.testing.assert_array_equal(st & F.POSE_OUTSIDE, st_ref)
+
+
+def test_world_frame_and_nearest(F):
+    field = uploaded_room_field(F)
+    poses = X.room_poses(1000)[:300]
+    fim, met, sg, st = run(F, field, poses, F.Q_METRICS | F.Q_WORLD)
+    I_ref, _ = oracle_query(poses, frame=O.FRAME_WORLD)
+    assert X.rel_fro(X.unpack21(fim), I_ref).max() <= X.TAU_F32
+    fim, met, sg, st = run(F, field, poses, F.Q_METRICS | F.Q_NEAREST)
+    I_ref, _ = oracle_query(poses, interp=O.INTERP_NEAREST)
+    assert X.rel_fro(X.unpack21(fim), I_ref).max() <= X.TAU_F32
+    check_metrics(I_ref, met, sg, X.TAU_F32)
+
+
+@pytest.mark.parametrize("m", [1, 31, 32, 33, 65])
+def test_ragged_batch_sizes(F, m):
+    field = uploaded_room_field(F)
+    poses = X.room_poses(1000)[:m]
+    fim, met, sg, st = run(F, field, poses)
+    I_ref, _ = oracle_query(poses)
+    assert X.rel_fro(X.unpack21(fim), I_ref).max() <= X.TAU_F32
+
+
+def test_edge_poses(F):
+    """Outside the lattice (clamped, status bit), exactly on the last node, a non-unit
+    quaternion (renormalised, status bit) and a NaN pose (NaN outputs, status bit)."""
+    field = uploaded_room_field(F)
+    poses = np.array([
+        [-1.0, 5.0, 1.0, 1, 0, 0, 0],
+        [10.0, 10.0, 3.0, 0.3, 0.5, -0.2, 0.7],
+        [4.2, 3.3, 1.1, 2.0, 0.0, 0.0, 0.0],
+        [np.nan, 1.0, 1.0, 1, 0, 0, 0],
+        [12.0, -3.0, 7.0, 0.1, 0.9, 0.3, -0.2],
+    ], np.float32)
+    fim, met, sg, st = run(F, field, poses)
+    I_ref, st_ref = oracle_query(poses[[0, 1, 2, 4]])
+    good = [0, 1, 2, 4]
+    assert X.rel_fro(X.unpack21(fim[good]), I_ref).max() <= X.TAU_F32
+    assert st[0] & F.POSE_OUTSIDE and st[4] & F.POSE_OUTSIDE
+    assert not (st[1] & F.POSE_OUTSIDE)
+    assert st[2] & F.POSE_QUAT
+    assert st[3] & F.POSE_NAN and np.all(np.isnan(fim[3])) and np.all(np.isnan(met[3]))
+
+
+def test_metric_subsets_and_optional_outputs(F):
+    field = uploaded_room_field(F)
+    poses = torch.from_numpy(X.room_poses(1000)[:100]).cuda()
+    fim_all, met_all, _, _ = field.query(poses, F.Q_METRICS)
+    met = torch.full((100, 3), -7.0, dtype=torch.float64, device="cuda")
+    F.query(field.c, poses, F.Q_TRACE, None, met, None, None)
+    torch.cuda.synchronize()
+    assert torch.equal(met[:, 0], met_all[:, 0])
+    assert torch.all(met[:, 1:] == -7.0)
+    fim = torch.empty(100, 21, device="cuda")
+    F.query(field.c, poses, 0, fim, None, None, None)
+    torch.cuda.synchronize()
+    assert torch.equal(fim, fim_all)
+
+
+def test_query_is_deterministic(F):
+    field = uploaded_room_field(F)
+    poses = torch.from_numpy(X.room_poses(1000)).cuda()
+    a = field.query(poses)
+    b = field.query(poses)
+    for x, y in zip(a, b):
+        assert torch.equal(x.nan_to_num(), y.nan_to_num())
