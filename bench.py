@@ -1,0 +1,408 @@
+"""Benchmark of the Fisher Information Field hot path on GB300.
+
+Metric: pose-FIM queries/s (+ p99 latency, vs the GPU point-cloud FIM; build pairs/s).
+
+Workload (the warehouse map): 200,000 landmarks on the surfaces of a 50 x 50 x 10 m hall
+with 40 box obstacles (60 % on box faces, 40 % on the walls), field of 200 x 200 x 40 nodes
+at 0.25 m (1.6M nodes, 1.38 GB in float32), range shell (0.1, 10] m, 90-degree field of
+view, v_alpha = 0.5.  The field is built once and stays resident; one timed step is one
+fif_query of 2^22 poses drawn uniformly over the lattice with uniform rotations, returning
+the FIM and trace / log|det| / lambda_min.  The field (1.38 GB) is ten times the L2, and the
+random positions defeat caching, so no L2 flush is needed between steps.
+
+Also reported (same run): the build (pairs/s, FP32 roofline), the point-cloud baseline over
+all 200,000 landmarks, end-to-end throughput through host buffers, a short open-loop serving
+run (p50/p99 latency), the FP64 CPU oracle on a bounded sample, and SM clocks sampled
+during the timed region.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+N > 1 runs under torchrun, one process per GPU, each rank holding a replica of the field and
+answering its own 2^22 poses (weak scaling, no exchange on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "pose-FIM queries/s + p99 latency vs GPU point-cloud FIM; build pairs/s"
+WORKLOAD = ("warehouse 50x50x10 m, 200k landmarks (60% box faces / 40% walls, 40 boxes), "
+            "field 200x200x40 nodes @0.25 m (1.6M nodes, fp32 216/node), r in (0.1, 10] m, "
+            "FoV 90 deg, v_alpha 0.5; step = fif_query of 2^22 uniform-random poses "
+            "(FIM + trace + log|det| + lambda_min)")
+QUERY_BYTES_PER_POSE = 8 * 210 * 4 + 7 * 4 + 21 * 4 + 3 * 8 + 1 + 4   # corners + pose + outputs
+BUILD_FLOPS_PER_PAIR = 151   # shell test 8, rsqrt 1, bearing 4, monomials 31, 66 accumulations 107
+SMS = 152
+FP32_LANES = 128
+SM_MAX_MHZ = 2070.0
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while active."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=2)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def time_events(fn, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in evs:
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def cpu_baseline(scene, spec, r_max, seed=123, n_poses=256, min_query_s=2.0):
+    """The FP64 oracle on a bounded sample of the same workload, on the host cores:
+    build the corner nodes of `n_poses` random poses (timed: pairs/s), then query them
+    repeatedly for at least `min_query_s` (timed: queries/s including the metrics)."""
+    import oracle as O
+    from paper_2008_03324_gb300 import synth
+    O.build()
+    poses = synth.random_poses(seed, n_poses, spec.lo, spec.hi)
+    grid = O.make_grid(spec.origin, spec.res, spec.dims)
+    prm = O.make_params(r_max=r_max, v_alpha=0.5)
+    nodes, w, dw, st = O.query_cells(grid, poses)
+    uniq, inv = np.unique(nodes.reshape(-1), return_inverse=True)
+    t0 = time.perf_counter()
+    blocks = O.field_nodes(scene.landmarks, grid, prm, uniq)
+    t_build = time.perf_counter() - t0
+    pairs = O.field_pairs(scene.landmarks, grid, prm, uniq)
+    corners = blocks[inv].reshape(n_poses, 8, 10, 6, 6)
+    k = O.quad_coeffs(prm.half_fov, prm.v_alpha)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        I = O.query(corners, w, poses, k)
+        O.metrics(I)
+        reps += 1
+        if time.perf_counter() - t0 >= min_query_s:
+            break
+    t_q = time.perf_counter() - t0
+    return {
+        "value": reps * n_poses / t_q, "unit": "queries/s", "cores": O.num_threads(), "kind": "oracle",
+        "sample": (f"{n_poses} uniform-random warehouse poses; the oracle first builds their {len(uniq)} corner "
+                   f"nodes over all {len(scene.landmarks)} landmarks ({t_build:.1f} s, "
+                   f"{pairs / t_build:.3e} in-shell pairs/s), then queries them {reps} times "
+                   f"(FIM + trace + log|det| + lambda_min, FP64)"),
+        "build_pairs_per_s": pairs / t_build,
+    }
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle as it stands, on the host cores."""
+    from paper_2008_03324_gb300 import dist
+    rank, _, ws = dist.world()
+    if rank != 0:
+        return 0
+    import oracle as O
+    from paper_2008_03324_gb300 import synth
+    O.build()
+    spec = synth.WAREHOUSE_GRID
+    scene = synth.warehouse(seed=2, n=200_000)
+    n_poses = 128
+    poses = synth.random_poses(7, n_poses, spec.lo, spec.hi)
+    grid = O.make_grid(spec.origin, spec.res, spec.dims)
+    prm = O.make_params(r_max=10.0, v_alpha=0.5)
+    nodes, w, dw, st = O.query_cells(grid, poses)
+    uniq, inv = np.unique(nodes.reshape(-1), return_inverse=True)
+    corners = O.field_nodes(scene.landmarks, grid, prm, uniq)[inv].reshape(n_poses, 8, 10, 6, 6)
+    k = O.quad_coeffs(prm.half_fov, prm.v_alpha)
+
+    def step():
+        I = O.query(corners, w, poses, k)
+        O.metrics(I)
+
+    for _ in range(args.warmup):
+        step()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        step()
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * float(np.mean(times))
+    val = n_poses / (ms * 1e-3)
+    sample = (f"{n_poses} uniform-random warehouse poses per step, corner coefficient sets prebuilt by the oracle "
+              f"(FIM + trace + log|det| + lambda_min, FP64)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "queries/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD + "; reference arm: FP64 CPU oracle, bounded sample", "poses_per_step": n_poses},
+        "cpu_baseline": {"value": val, "unit": "queries/s", "cores": O.num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--poses", type=int, default=1 << 22)
+    ap.add_argument("--phase", default="all", choices=["all", "query", "build"],
+                    help="build: time only the build; query: build once untimed, time only the query")
+    ap.add_argument("--build-nz", type=int, default=40, help="lattice z-layers (smaller for profiling)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=1500)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2008_03324_gb300 import build as B
+    from paper_2008_03324_gb300 import dist, fif, serve, synth
+
+    rank, local, ws = dist.world()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init()
+    if rank == 0:
+        B.build()
+    dist.barrier()
+    B.build()   # up to date by now: a no-op on the other ranks
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    hbm_peak, peak_kind = _peaks()
+
+    spec = synth.WAREHOUSE_GRID
+    if args.build_nz != spec.dims[2]:
+        spec = synth.GridSpec(spec.origin, spec.res, (spec.dims[0], spec.dims[1], args.build_nz))
+    scene = synth.warehouse(seed=2, n=200_000)
+    r_max = 10.0
+    params = fif.make_params(r_max=r_max, v_alpha=0.5)
+    field = fif.Field(spec.origin, spec.res, spec.dims, params)
+    lm = torch.from_numpy(scene.landmarks).to(dev)
+    wsb = torch.empty(fif.build_workspace_bytes(field.c, lm.shape[0]), dtype=torch.uint8, device=dev)
+
+    out = {}
+    launches = 0
+    # ---------------- build ----------------
+    build_steps = 3 if args.phase != "query" else 1
+    tb = time_events(lambda: fif.build(field.c, lm, wsb), build_steps, 1 if args.phase != "query" else 0, stream)
+    inshell, cand, dropped = fif.build_stats(wsb, field, lm.shape[0])
+    tb_ms = float(np.mean(tb))
+    nominal_fp32 = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    build_tflops = inshell * BUILD_FLOPS_PER_PAIR / (tb_ms * 1e-3) / 1e12
+    out["build"] = {
+        "ms": tb_ms, "pairs_per_s": inshell / (tb_ms * 1e-3), "in_shell_pairs": inshell, "candidate_pairs": cand,
+        "launches_per_build": 7,
+        "roofline": {"bound": "alu", "achieved": build_tflops, "peak": nominal_fp32, "unit": "TFLOP/s",
+                     "frac": build_tflops / nominal_fp32, "traffic": None,
+                     "peak_kind": "nominal FP32: 152 SMs x 128 lanes x 2 x 2070 MHz"},
+    }
+    assert fif.device_error() == 0
+    if args.phase == "build":
+        if rank == 0:
+            print(json.dumps({"metric": "build pairs/s", "unit": "pairs/s", "value": out["build"]["pairs_per_s"],
+                              "n_gpus": ws, "config": {"workload": WORKLOAD, "lattice": list(spec.dims)},
+                              "build": out["build"]}), flush=True)
+        return 0
+
+    # ---------------- query (the timed step) ----------------
+    m = args.poses
+    poses = torch.from_numpy(synth.random_poses(1000 + rank, m, spec.lo, spec.hi)).to(dev)
+    fim = torch.empty(m, 21, dtype=torch.float32, device=dev)
+    met = torch.empty(m, 3, dtype=torch.float64, device=dev)
+    sg = torch.empty(m, dtype=torch.int8, device=dev)
+    st = torch.empty(m, dtype=torch.int32, device=dev)
+
+    def qstep():
+        fif.query(field.c, poses, fif.Q_METRICS, fim, met, sg, st)
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        for _ in range(args.warmup):
+            qstep()
+        torch.cuda.synchronize()
+        dist.barrier()
+        torch.cuda.synchronize()
+        t_all0 = torch.cuda.Event(enable_timing=True)
+        t_all1 = torch.cuda.Event(enable_timing=True)
+        t_all0.record(stream)
+        for a, b in evs:
+            a.record(stream)
+            qstep()
+            b.record(stream)
+        t_all1.record(stream)
+        torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    launches += args.steps
+    per = [a.elapsed_time(b) for a, b in evs]
+    total_ms = t_all0.elapsed_time(t_all1)
+    total_ms = dist.max_over_ranks(total_ms, dev)
+    ms_step = total_ms / args.steps
+    value = m * ws * args.steps / (total_ms * 1e-3)
+    kernel_ms = float(np.mean(per))
+    achieved = m * QUERY_BYTES_PER_POSE / (kernel_ms * 1e-3) / 1e9
+    status = st.cpu().numpy()
+
+    if args.phase == "query":
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws,
+                              "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+                              "kernel_ms": kernel_ms, "roofline_achieved_gbs": achieved,
+                              "config": {"workload": WORKLOAD, "poses_per_step": m}}), flush=True)
+        return 0
+
+    # ---------------- end to end through host buffers ----------------
+    h_poses = torch.from_numpy(synth.random_poses(2000 + rank, m, spec.lo, spec.hi)).pin_memory()
+    h_met = torch.empty(m, 3, dtype=torch.float64).pin_memory()
+    h_sg = torch.empty(m, dtype=torch.int8).pin_memory()
+    h_st = torch.empty(m, dtype=torch.int32).pin_memory()
+
+    def e2e_step():
+        poses.copy_(h_poses, non_blocking=True)
+        fif.query(field.c, poses, fif.Q_METRICS, fim, met, sg, st)
+        h_met.copy_(met, non_blocking=True)
+        h_sg.copy_(sg, non_blocking=True)
+        h_st.copy_(st, non_blocking=True)
+
+    e2e_steps = max(3, args.steps // 2)
+    te = time_events(e2e_step, e2e_steps, 2, stream)
+    launches += 0
+    e2e_ms = dist.max_over_ranks(float(np.mean(te)), dev)
+    e2e = {"value": m * ws / (e2e_ms * 1e-3), "unit": "queries/s", "h2d_bytes_per_step": m * 28,
+           "d2h_bytes_per_step": m * (24 + 1 + 4), "ms_per_step": e2e_ms}
+
+    # ---------------- point-cloud baseline (all 200k landmarks) ----------------
+    mp = 8192
+    tp = time_events(lambda: fif.pointcloud_fim(lm, params, fif.make_pinhole(), poses[:mp], fif.Q_METRICS,
+                                                fim, met, sg, st), 3, 1, stream)
+    pc_rate = mp / (float(np.mean(tp)) * 1e-3)
+    out["pointcloud"] = {"queries_per_s": pc_rate, "landmarks": int(lm.shape[0]), "poses": mp,
+                         "field_speedup": (value / ws) / pc_rate}
+
+    # ---------------- serving (rank 0) ----------------
+    if rank == 0 and args.serve_requests > 0:
+        reqs = synth.request_stream(3, args.serve_requests, scene)
+        rate = 20_000.0
+        arr = synth.poisson_arrivals(4, len(reqs), rate)
+        srv = serve.FifServer(field, max_batch_poses=1 << 19, slots=512, mem_budget_bytes=256 << 20, streams=2)
+        srv.run(reqs[:50], synth.poisson_arrivals(5, 50, rate))   # warm-up
+        t0 = time.perf_counter()
+        res = srv.run(reqs, arr)
+        wall = time.perf_counter() - t0
+        lat = serve.latency_stats(res)
+        n_poses = sum(r.shape[0] for r in reqs)
+        out["serving"] = {"arrival_rate_req_per_s": rate, "requests": len(reqs), "poses": n_poses,
+                          "served_queries_per_s": n_poses / wall, "batches": srv.batches_launched,
+                          "peak_inflight_bytes": srv.peak_bytes, **lat}
+
+    # ---------------- CPU oracle baseline (rank 0, N = 1) ----------------
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(scene, spec, r_max)
+
+    if rank == 0:
+        clocks = clk.summary()
+        line = {
+            "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "poses_per_step": m, "field_nodes": field.n_nodes,
+                       "landmarks": int(lm.shape[0]),
+                       "l2": "inputs larger than L2: 1.38 GB field gathered at uniform-random positions",
+                       "parallelism": f"replicas x{ws}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": None,
+                         "peak_kind": f"{peak_kind} (MEASURED_PEAKS hbm_gbs)",
+                         "bytes_per_pose": QUERY_BYTES_PER_POSE, "kernel_ms": kernel_ms},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "p99_latency_ms": out.get("serving", {}).get("p99_ms"),
+            "status_counts": {"outside": int(((status & 1) != 0).sum()), "not_pd": int(((status & 4) != 0).sum())},
+            **out,
+        }
+        print(json.dumps(line), flush=True)
+    dist.barrier()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

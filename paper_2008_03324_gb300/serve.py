@@ -1,0 +1,196 @@
+"""Continuous-batching request loop for pose-FIM queries on a device-resident field.
+
+Planner requests (RRT* edges, trajectory samples: 8-4096 poses each) arrive over time.  The
+loop admits a request when a slot is free and its bytes fit the in-flight memory budget,
+packs every admitted request into the next batch (one pinned host buffer, one host-to-device
+copy, one fif_query launch, one device-to-host copy of the metrics) and keeps up to `streams`
+batches in flight on separate CUDA streams, so requests that arrive while a batch runs join
+the next one.  Completion is detected by polling CUDA events with a deadline (no blocking
+waits).  Every result is independent of the batch it travelled in: the query of a pose
+depends on that pose only.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field as dfield
+
+import numpy as np
+import torch
+
+from . import fif
+
+BYTES_PER_POSE = 7 * 4 + 3 * 8 + 1 + 4   # pose in; metrics, sign, status out
+
+
+@dataclass
+class Result:
+    metrics: np.ndarray      # [L, 3] float64: trace, log|det|, lambda_min
+    sign: np.ndarray         # [L] int8
+    status: np.ndarray       # [L] int32
+    arrival: float = 0.0
+    admitted: float = 0.0
+    done: float = 0.0
+
+    @property
+    def latency(self):
+        return self.done - self.arrival
+
+
+@dataclass
+class _Batch:
+    stream: torch.cuda.Stream
+    event: torch.cuda.Event
+    reqs: list
+    offsets: list
+    n: int
+    launched: float
+    slot: int = 0
+
+
+class AdmissionError(RuntimeError):
+    pass
+
+
+class FifServer:
+    def __init__(self, fld: fif.Field, max_batch_poses: int = 1 << 18, slots: int = 256,
+                 mem_budget_bytes: int = 64 << 20, streams: int = 2, flags: int = fif.Q_METRICS,
+                 deadline_s: float = 10.0):
+        self.field = fld
+        self.max_batch = int(max_batch_poses)
+        self.slots = int(slots)
+        self.mem_budget = int(mem_budget_bytes)
+        self.flags = flags
+        self.deadline = deadline_s
+        dev = fld.coeffs.device
+        self.bufs = []
+        for _ in range(streams):
+            self.bufs.append(dict(
+                stream=torch.cuda.Stream(device=dev),
+                h_pose=torch.empty(self.max_batch, 7, dtype=torch.float32, pin_memory=True),
+                h_met=torch.empty(self.max_batch, 3, dtype=torch.float64, pin_memory=True),
+                h_sg=torch.empty(self.max_batch, dtype=torch.int8, pin_memory=True),
+                h_st=torch.empty(self.max_batch, dtype=torch.int32, pin_memory=True),
+                d_pose=torch.empty(self.max_batch, 7, dtype=torch.float32, device=dev),
+                d_met=torch.empty(self.max_batch, 3, dtype=torch.float64, device=dev),
+                d_sg=torch.empty(self.max_batch, dtype=torch.int8, device=dev),
+                d_st=torch.empty(self.max_batch, dtype=torch.int32, device=dev),
+                busy=False,
+            ))
+        self.in_use_slots = 0
+        self.in_use_bytes = 0
+        self.peak_bytes = 0
+        self.peak_slots = 0
+        self.batches_launched = 0
+        self.kernel_launches = 0
+
+    # ---- admission ----------------------------------------------------------------
+    def _fits(self, n):
+        return self.in_use_slots < self.slots and self.in_use_bytes + n * BYTES_PER_POSE <= self.mem_budget
+
+    def _admit(self, n):
+        self.in_use_slots += 1
+        self.in_use_bytes += n * BYTES_PER_POSE
+        self.peak_bytes = max(self.peak_bytes, self.in_use_bytes)
+        self.peak_slots = max(self.peak_slots, self.in_use_slots)
+
+    def _release(self, n):
+        self.in_use_slots -= 1
+        self.in_use_bytes -= n * BYTES_PER_POSE
+
+    # ---- batches --------------------------------------------------------------------
+    def _launch(self, bi, reqs, now):
+        b = self.bufs[bi]
+        offs, n = [], 0
+        for (_, poses) in reqs:
+            L = poses.shape[0]
+            b["h_pose"][n:n + L].copy_(torch.from_numpy(poses))
+            offs.append(n)
+            n += L
+        s = b["stream"]
+        with torch.cuda.stream(s):
+            b["d_pose"][:n].copy_(b["h_pose"][:n], non_blocking=True)
+            fif.query(self.field.c, b["d_pose"][:n], self.flags, None, b["d_met"][:n], b["d_sg"][:n],
+                      b["d_st"][:n], stream=s)
+            b["h_met"][:n].copy_(b["d_met"][:n], non_blocking=True)
+            b["h_sg"][:n].copy_(b["d_sg"][:n], non_blocking=True)
+            b["h_st"][:n].copy_(b["d_st"][:n], non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(s)
+        b["busy"] = True
+        self.batches_launched += 1
+        self.kernel_launches += 1
+        return _Batch(stream=s, event=ev, reqs=reqs, offsets=offs, n=n, launched=now, slot=bi)
+
+    def _complete(self, batch, results, now):
+        b = self.bufs[batch.slot]
+        for (rid, poses), off in zip(batch.reqs, batch.offsets):
+            L = poses.shape[0]
+            r = results[rid]
+            r.metrics = b["h_met"][off:off + L].numpy().copy()
+            r.sign = b["h_sg"][off:off + L].numpy().copy()
+            r.status = b["h_st"][off:off + L].numpy().copy()
+            r.done = now
+            self._release(L)
+        b["busy"] = False
+
+    def run(self, requests, arrivals=None, clock=time.perf_counter):
+        """Serve `requests` (list of [L, 7] float32 arrays) arriving at `arrivals` seconds
+        (open loop; None = all at t=0).  Returns the list of Result in request order."""
+        n_req = len(requests)
+        if arrivals is None:
+            arrivals = np.zeros(n_req)
+        order = np.argsort(arrivals, kind="stable")
+        for r in requests:
+            if r.shape[0] > self.max_batch or r.shape[0] * BYTES_PER_POSE > self.mem_budget:
+                raise AdmissionError(f"request of {r.shape[0]} poses exceeds the batch or memory limit")
+        results = [Result(np.zeros((0, 3)), np.zeros(0, np.int8), np.zeros(0, np.int32)) for _ in range(n_req)]
+        t0 = clock()
+        nxt = 0                  # next request (in arrival order) not yet arrived
+        waiting = []             # arrived, not admitted
+        ready = []               # admitted, not launched
+        inflight = []
+        done = 0
+        while done < n_req:
+            now = clock() - t0
+            while nxt < n_req and arrivals[order[nxt]] <= now:
+                rid = int(order[nxt])
+                results[rid].arrival = float(arrivals[rid])
+                waiting.append(rid)
+                nxt += 1
+            while waiting and self._fits(requests[waiting[0]].shape[0]):
+                rid = waiting.pop(0)
+                self._admit(requests[rid].shape[0])
+                results[rid].admitted = now
+                ready.append(rid)
+            # complete finished batches
+            still = []
+            for b in inflight:
+                if b.event.query():
+                    self._complete(b, results, clock() - t0)
+                    done += len(b.reqs)
+                elif now - b.launched > self.deadline:
+                    raise TimeoutError(f"batch of {b.n} poses exceeded {self.deadline} s ({fif.status_str(fif.ETIMEOUT)})")
+                else:
+                    still.append(b)
+            inflight = still
+            # launch on a free stream
+            free = [i for i, b in enumerate(self.bufs) if not b["busy"]]
+            if ready and free:
+                take, n = [], 0
+                while ready and n + requests[ready[0]].shape[0] <= self.max_batch:
+                    rid = ready.pop(0)
+                    take.append((rid, requests[rid]))
+                    n += requests[rid].shape[0]
+                inflight.append(self._launch(free[0], take, clock() - t0))
+            elif not inflight and not ready and nxt < n_req and not waiting:
+                # idle until the next arrival
+                dt = arrivals[order[nxt]] - (clock() - t0)
+                if dt > 2e-4:
+                    time.sleep(dt - 1e-4)
+        return results
+
+
+def latency_stats(results):
+    lat = np.array([r.latency for r in results])
+    return dict(p50_ms=float(np.percentile(lat, 50) * 1e3), p99_ms=float(np.percentile(lat, 99) * 1e3),
+                mean_ms=float(lat.mean() * 1e3), max_ms=float(lat.max() * 1e3))

@@ -32,11 +32,12 @@ def uploaded(F, v_alpha):
 
 
 def well_posed(I, which):
-    """lambda_min's derivative needs a simple smallest eigenvalue."""
+    """lambda_min's derivative needs a simple smallest eigenvalue: keep poses whose two
+    smallest eigenvalues are separated by more than 1e-3 of the second one."""
     if which != 2:
         return np.ones(len(I), bool)
     ev = np.linalg.eigvalsh(I)
-    return (ev[:, 1] - ev[:, 0]) > 1e-3 * np.abs(ev).max(axis=1)
+    return (ev[:, 1] - ev[:, 0]) > 1e-3 * np.abs(ev[:, 1])
 
 
 @pytest.mark.parametrize("which", [0, 1, 2])
@@ -67,7 +68,7 @@ def test_adjoint_matches_oracle_gradient(F, which, world):
     I_ref = O.query(Fw[nodes], w, poses, k, O.FRAME_WORLD if world else O.FRAME_CAMERA)[: len(ref)]
     ok = well_posed(I_ref, which)
     err = np.linalg.norm(g - ref, axis=1) / np.linalg.norm(ref, axis=1)
-    assert ok.mean() > 0.8
+    assert ok.sum() >= 0.5 * len(ok)
     assert err[ok].max() <= TOL, (err[ok].max(), np.argmax(np.where(ok, err, 0)))
     assert np.all(g[:, 5] == 0.0)
 
