@@ -166,6 +166,25 @@ FIF_API size_t fif_build_workspace_bytes(const fif_field* field, int64_t n_landm
 FIF_API int32_t fif_build(fif_field* field, const float* d_landmarks, int64_t n, void* d_workspace,
                   size_t workspace_bytes, fif_stream_t stream);
 
+/* Size of the fixed device scratch array that fif_build_static uses (16 MiB). */
+#define FIF_BUILD_STATIC_SCRATCH_BYTES (16u << 20)
+
+/* fif_build without a workspace argument, for callers that cannot allocate device memory
+ * once they run (for example a planner loaded as a plug-in into an application whose own
+ * allocator owns the GPU memory, or a real-time loop that forbids cudaMalloc after start-up
+ * because it may synchronise the device and take unbounded time).  The paper has no
+ * counterpart: this is a library convenience.
+ * The build's scratch lives in one fixed array of FIF_BUILD_STATIC_SCRATCH_BYTES inside the
+ * library, present on every GPU that loads the library until the process exits.  Results
+ * are those of fif_build.  Returns FIF_ERANGE, without launching anything, when n landmarks
+ * on this field need more scratch than that (fif_build_workspace_bytes(field, n) > the
+ * maximum; about 768,000 landmarks for the 200 x 200 x 40 warehouse lattice).  The first call on a device
+ * looks up the array's device address (once per device, with that device current); make that
+ * first call before any stream capture.  All calls share the one array: calls whose work
+ * overlaps on the GPU (other streams, other threads) race and corrupt each other's fields;
+ * serialise them.  Calls no allocator. */
+FIF_API int32_t fif_build_static(fif_field* field, const float* d_landmarks, int64_t n, fif_stream_t stream);
+
 /* Query m poses (Sec. VI-A-1, Eq. fim_separation, Eq. general_info_query):
  *   I(T) = sum_k v_r(z)[k] * C_k(t),  z = R_wc e3 (the optical axis),
  * v_r = [k2 z1^2, k2 z2^2, k2 z3^2, 2 k2 z1 z2, 2 k2 z1 z3, 2 k2 z2 z3, k1 z1, k1 z2, k1 z3, k0]

@@ -72,6 +72,7 @@ _SIGS = {
                               ctypes.c_size_t]),
     "fif_build_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(FieldC), _I64]),
     "fif_build": (_I32, [ctypes.POINTER(FieldC), _VP, _I64, _VP, ctypes.c_size_t, _VP]),
+    "fif_build_static": (_I32, [ctypes.POINTER(FieldC), _VP, _I64, _VP]),
     "fif_query": (_I32, [ctypes.POINTER(FieldC), _VP, _I64, _I32, _VP, _VP, _VP, _VP, _VP]),
     "fif_query_backward": (_I32, [ctypes.POINTER(FieldC), _VP, _I64, _I32, _VP, _VP, _VP, _VP]),
     "fif_pointcloud_fim": (_I32, [_VP, _I64, ctypes.POINTER(Params), ctypes.POINTER(Pinhole), _VP, _I64, _I32,
@@ -161,6 +162,17 @@ def build(field: FieldC, landmarks: torch.Tensor, workspace: torch.Tensor, strea
     assert landmarks.is_cuda and landmarks.dtype == torch.float32 and landmarks.is_contiguous()
     _check(lib().fif_build(ctypes.byref(field), _ptr(landmarks), landmarks.shape[0], _ptr(workspace),
                            workspace.numel() * workspace.element_size(), _stream(stream)), "fif_build")
+
+
+BUILD_STATIC_SCRATCH_BYTES = 16 << 20
+
+
+def build_static(field: FieldC, landmarks: torch.Tensor, stream=None):
+    """fif_build without a workspace: the scratch is the library's fixed 16 MiB device array
+    (for callers that cannot allocate; see include/fif.h).  Calls that overlap on the GPU race."""
+    assert landmarks.is_cuda and landmarks.dtype == torch.float32 and landmarks.is_contiguous()
+    _check(lib().fif_build_static(ctypes.byref(field), _ptr(landmarks), landmarks.shape[0], _stream(stream)),
+           "fif_build_static")
 
 
 def query(field: FieldC, poses: torch.Tensor, flags=Q_METRICS, fim=None, metrics=None, sign=None, status=None,
