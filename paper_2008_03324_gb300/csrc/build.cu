@@ -29,6 +29,7 @@
 #include "fif_internal.h"
 
 #include <cmath>
+#include <cstring>
 
 namespace fif {
 
@@ -54,6 +55,34 @@ __device__ __constant__ int8_t kVp[10][3] = {{2, 0, 0}, {0, 2, 0}, {0, 0, 2}, {1
                                              {0, 1, 1}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {0, 0, 0}};
 // moment blocks: base index of (power of 1/n, degree)
 constexpr int kS4n2 = 0, kS3n2 = 15, kS3n1 = 25, kS2n1 = 35, kS4n0 = 41, kS3n0 = 56;
+
+// packed single-precision pairs (sm_100+ f32x2 instructions: one issue slot, two lanes' worth
+// of FP32 work; each half rounds exactly like the scalar instruction)
+__device__ __forceinline__ unsigned long long pk2(float2 v) {
+    unsigned long long u;
+    memcpy(&u, &v, 8);
+    return u;
+}
+__device__ __forceinline__ float2 upk2(unsigned long long u) {
+    float2 v;
+    memcpy(&v, &u, 8);
+    return v;
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
+    return upk2(d);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
+    return upk2(d);
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)), "l"(pk2(c)));
+    return upk2(d);
+}
 
 // ------------------------------------------------------------------------------------
 // binning
@@ -301,9 +330,21 @@ __global__ void __launch_bounds__(kThreads, 2) build_kernel(BuildArgs a) {
 
     // ---- consume ----
     const float rmin2 = a.rmin2, rmax2 = a.rmax2;
-    float acc[kMom];
+    // register block of the 66 moment sums, in packed pairs following the moment order:
+    // S4n2 (15) = 7 pairs + 1, S3n2 (10) = 5, S3n1 (10) = 5, S2n1 (6) = 3, S4n0 (15) = 7 + 1,
+    // S3n0 (10) = 5
+    float2 a4n2[7], a3n2[5], a3n1[5], a2n1[3], a4n0[7], a3n0[5];
+    float a4n2_14, a4n0_14;
+    auto zero_block = [&]() {
 #pragma unroll
-    for (int i = 0; i < kMom; ++i) acc[i] = 0.f;
+        for (int i = 0; i < 7; ++i) a4n2[i] = a4n0[i] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) a3n2[i] = a3n1[i] = a3n0[i] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) a2n1[i] = make_float2(0.f, 0.f);
+        a4n2_14 = a4n0_14 = 0.f;
+    };
+    zero_block();
     float* hs = &S.hi[0][0];
     float* ls = &S.lo[0][0];
     unsigned int in_pairs = 0;
@@ -333,32 +374,66 @@ __global__ void __launch_bounds__(kThreads, 2) build_kernel(BuildArgs a) {
                 in_pairs += in ? 1u : 0u;
                 const float r = rsqrtf(n2);
                 const float inv_n = in ? r : 0.f;
-                const float x = dx * inv_n, y = dy * inv_n, z = dz * inv_n;
+                const float2 xy = mul2(make_float2(dx, dy), make_float2(inv_n, inv_n));
+                const float x = xy.x, y = xy.y, z = dz * inv_n;
                 const float w2 = inv_n * inv_n;
-                const float xx = x * x, yy = y * y, zz = z * z, xy = x * y, xz = x * z, yz = y * z;
-                const float m3[10] = {xx * x, yy * y, zz * z, xx * y, xx * z, yy * x, yy * z, zz * x, zz * y, xy * z};
-                const float m4[15] = {xx * xx, yy * yy, zz * zz, xx * xy, xx * xz, yy * xy, yy * yz, zz * xz,
-                                      zz * yz, xx * yy, xx * zz, yy * zz, xx * yz, yy * xz, zz * xy};
-                const float m2[6] = {xx, yy, zz, xy, xz, yz};
+                const float2 vw2 = make_float2(w2, w2), vn = make_float2(inv_n, inv_n);
+                // degree 2: (xx, yy) (zz, xy) (xz, yz)
+                const float2 m2a = mul2(make_float2(x, y), make_float2(x, y));
+                const float2 m2b = mul2(make_float2(z, x), make_float2(z, y));
+                const float2 m2c = mul2(make_float2(x, y), make_float2(z, z));
+                const float xx = m2a.x, yy = m2a.y, zz = m2b.x, xyv = m2b.y, xz = m2c.x, yz = m2c.y;
+                // degree 3: (xxx, yyy) (zzz, xxy) (xxz, xyy) (yyz, xzz) (yzz, xyz)
+                const float2 m3a = mul2(m2a, make_float2(x, y));
+                const float2 m3b = mul2(make_float2(zz, xx), make_float2(z, y));
+                const float2 m3c = mul2(make_float2(xx, xyv), make_float2(z, y));
+                const float2 m3d = mul2(make_float2(yy, xz), make_float2(z, z));
+                const float2 m3e = mul2(make_float2(yz, xyv), make_float2(z, z));
+                // degree 4: (xxxx, yyyy) (zzzz, xxxy) (xxxz, xyyy) (yyyz, xzzz) (yzzz, xxyy)
+                //           (xxzz, yyzz) (xxyz, xyyz) xyzz
+                const float2 m4a = mul2(m2a, m2a);
+                const float2 m4b = mul2(make_float2(zz, xx), make_float2(zz, xyv));
+                const float2 m4c = mul2(make_float2(xx, yy), make_float2(xz, xyv));
+                const float2 m4d = mul2(make_float2(yy, zz), make_float2(yz, xz));
+                const float2 m4e = mul2(make_float2(zz, xx), make_float2(yz, yy));
+                const float2 m4f = mul2(make_float2(xx, yy), make_float2(zz, zz));
+                const float2 m4g = mul2(make_float2(xx, yy), make_float2(yz, xz));
+                const float m4h = zz * xyv;
+                const float2 m4[7] = {m4a, m4b, m4c, m4d, m4e, m4f, m4g};
+                const float2 m3[5] = {m3a, m3b, m3c, m3d, m3e};
+                const float2 m2[3] = {m2a, m2b, m2c};
 #pragma unroll
-                for (int i = 0; i < 15; ++i) acc[kS4n2 + i] = fmaf(m4[i], w2, acc[kS4n2 + i]);
+                for (int i = 0; i < 7; ++i) a4n2[i] = fma2(m4[i], vw2, a4n2[i]);
+                a4n2_14 = fmaf(m4h, w2, a4n2_14);
 #pragma unroll
-                for (int i = 0; i < 10; ++i) acc[kS3n2 + i] = fmaf(m3[i], w2, acc[kS3n2 + i]);
+                for (int i = 0; i < 5; ++i) a3n2[i] = fma2(m3[i], vw2, a3n2[i]);
 #pragma unroll
-                for (int i = 0; i < 10; ++i) acc[kS3n1 + i] = fmaf(m3[i], inv_n, acc[kS3n1 + i]);
+                for (int i = 0; i < 5; ++i) a3n1[i] = fma2(m3[i], vn, a3n1[i]);
 #pragma unroll
-                for (int i = 0; i < 6; ++i) acc[kS2n1 + i] = fmaf(m2[i], inv_n, acc[kS2n1 + i]);
+                for (int i = 0; i < 3; ++i) a2n1[i] = fma2(m2[i], vn, a2n1[i]);
 #pragma unroll
-                for (int i = 0; i < 15; ++i) acc[kS4n0 + i] += m4[i];
+                for (int i = 0; i < 7; ++i) a4n0[i] = add2(a4n0[i], m4[i]);
+                a4n0_14 += m4h;
 #pragma unroll
-                for (int i = 0; i < 10; ++i) acc[kS3n0 + i] += m3[i];
+                for (int i = 0; i < 5; ++i) a3n0[i] = add2(a3n0[i], m3[i]);
             }
-            // compensated merge of the block sums
+            // compensated merge of the block sums (moment order)
+            auto merge2 = [&](int base, const float2* v, int npairs) {
 #pragma unroll
-            for (int i = 0; i < kMom; ++i) {
-                kahan_merge(hs, ls, i * kThreads + tid, acc[i]);
-                acc[i] = 0.f;
-            }
+                for (int i = 0; i < npairs; ++i) {
+                    kahan_merge(hs, ls, (base + 2 * i) * kThreads + tid, v[i].x);
+                    kahan_merge(hs, ls, (base + 2 * i + 1) * kThreads + tid, v[i].y);
+                }
+            };
+            merge2(kS4n2, a4n2, 7);
+            kahan_merge(hs, ls, (kS4n2 + 14) * kThreads + tid, a4n2_14);
+            merge2(kS3n2, a3n2, 5);
+            merge2(kS3n1, a3n1, 5);
+            merge2(kS2n1, a2n1, 3);
+            merge2(kS4n0, a4n0, 7);
+            kahan_merge(hs, ls, (kS4n0 + 14) * kThreads + tid, a4n0_14);
+            merge2(kS3n0, a3n0, 5);
+            zero_block();
         }
         __syncthreads();  // everyone is done with this slot
         if (tid == 0) {

@@ -170,13 +170,14 @@ FIF_DEV void logdet_f64(const float* s, double& logabs, int& sign) {
     bool zero = false;
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
-        // pivot search over rows c..5
+        // pivot search over rows c..5 (on single-precision magnitudes: the choice only
+        // affects stability, and the comparisons stay off the slow double-precision pipe)
         int p = c;
-        double best = fabs(a[c][c]);
+        float best = fabsf((float)a[c][c]);
 #pragma unroll
         for (int r = 0; r < 6; ++r) {
             if (r <= c) continue;
-            const double v = fabs(a[r][c]);
+            const float v = fabsf((float)a[r][c]);
             if (v > best) { best = v; p = r; }
         }
         // exchange rows c and p with selects
@@ -214,67 +215,101 @@ FIF_DEV void logdet_f64(const float* s, double& logabs, int& sign) {
     sign = sg;
 }
 
-// Smallest eigenvalue of a symmetric 6x6 (packed, float): cyclic Jacobi in single precision
-// (fixed number of sweeps, all in registers) gives the eigenvector x; the eigenvalue is then
-// the Rayleigh quotient x^T S x / x^T x evaluated in double precision (its error is second
-// order in the eigenvector error).  If want_vec, x (unit, float) is returned too.
-template <int SWEEPS = 6>
-FIF_DEV double lambda_min_f64(const float* s, float* xout = nullptr) {
-    float a[21];
+// ---- smallest eigenvalue ------------------------------------------------------------
+// Jacobi rotation (t = tan, c = cos, s = sin) that zeroes a_pq of a symmetric 2x2 block,
+// with the convention a'_rp = c a_rp - s a_rq, a'_rq = s a_rp + c a_rq.  Fast intrinsics:
+// the angle only has to reduce the off-diagonal mass, not be correctly rounded.
+FIF_DEV void jacobi_angle(float app, float aqq, float apq, float& t, float& c, float& s) {
+    const float theta = __fdividef(aqq - app, 2.f * apq);
+    const float h = fmaf(theta, theta, 1.f);
+    const float root = h * rsqrtf(h);
+    float tt = copysignf(__fdividef(1.f, fabsf(theta) + root), theta);
+    const bool skip = !(fabsf(apq) > 1e-30f * (fabsf(app) + fabsf(aqq))) || !isfinite(tt);
+    tt = skip ? 0.f : tt;
+    t = tt;
+    c = rsqrtf(fmaf(tt, tt, 1.f));
+    s = tt * c;
+}
+
+// One round of the parallel (Brent-Luk) ordering for n = 6: three rotations on disjoint index
+// pairs, whose angles all come from the current matrix, applied together as A <- J^T A J,
+// V <- V J.  Three independent dependency chains per round instead of one.
+template <int p0, int q0, int p1, int q1, int p2, int q2>
+FIF_DEV void jacobi_round(float (&a)[6][6], float (&V)[6][6]) {
+    constexpr int P[3] = {p0, p1, p2}, Q[3] = {q0, q1, q2};
+    float t[3], c[3], s[3];
 #pragma unroll
-    for (int i = 0; i < 21; ++i) a[i] = s[i];
-    float V[6][6];
+    for (int k = 0; k < 3; ++k) jacobi_angle(a[P[k]][P[k]], a[Q[k]][Q[k]], a[P[k]][Q[k]], t[k], c[k], s[k]);
+    // blocks between two different pairs: X' = J_k^T X J_l
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int l = k + 1; l < 3; ++l) {
+            const int p = P[k], q = Q[k], u = P[l], v = Q[l];
+            // columns (pair l)
+            const float xpu = c[l] * a[p][u] - s[l] * a[p][v], xpv = s[l] * a[p][u] + c[l] * a[p][v];
+            const float xqu = c[l] * a[q][u] - s[l] * a[q][v], xqv = s[l] * a[q][u] + c[l] * a[q][v];
+            // rows (pair k)
+            const float ypu = c[k] * xpu - s[k] * xqu, yqu = s[k] * xpu + c[k] * xqu;
+            const float ypv = c[k] * xpv - s[k] * xqv, yqv = s[k] * xpv + c[k] * xqv;
+            a[p][u] = a[u][p] = ypu;
+            a[p][v] = a[v][p] = ypv;
+            a[q][u] = a[u][q] = yqu;
+            a[q][v] = a[v][q] = yqv;
+        }
+    // diagonal blocks
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int p = P[k], q = Q[k];
+        const float apq = a[p][q];
+        a[p][p] = a[p][p] - t[k] * apq;
+        a[q][q] = a[q][q] + t[k] * apq;
+        a[p][q] = a[q][p] = 0.f;
+    }
 #pragma unroll
     for (int r = 0; r < 6; ++r)
 #pragma unroll
-        for (int c = 0; c < 6; ++c) V[r][c] = (r == c) ? 1.f : 0.f;
+        for (int k = 0; k < 3; ++k) {
+            const float vp = V[r][P[k]], vq = V[r][Q[k]];
+            V[r][P[k]] = c[k] * vp - s[k] * vq;
+            V[r][Q[k]] = s[k] * vp + c[k] * vq;
+        }
+}
+
+// Smallest eigenvalue of a symmetric 6x6 (packed, float): parallel-ordered Jacobi in single
+// precision gives the eigenvector x of the smallest diagonal; the eigenvalue is the Rayleigh
+// quotient x^T S x / x^T x in double precision (its error is second order in the error of x).
+// If xout is given, x (unit, float) is returned too.
+template <int SWEEPS = 4>
+FIF_DEV double lambda_min_f64(const float* s, float* xout = nullptr) {
+    float a[6][6], V[6][6];
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            a[r][c] = s[sym_idx(r, c)];
+            V[r][c] = (r == c) ? 1.f : 0.f;
+        }
 #pragma unroll 1
     for (int sweep = 0; sweep < SWEEPS; ++sweep) {
-#pragma unroll
-        for (int p = 0; p < 5; ++p)
-#pragma unroll
-            for (int q = p + 1; q < 6; ++q) {
-                const float apq = a[sym_idx(p, q)];
-                const float app = a[sym_idx(p, p)], aqq = a[sym_idx(q, q)];
-                // t = tan of the rotation angle, smaller root
-                float theta = (aqq - app) / (2.f * apq);
-                float t = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.f)));
-                t = (fabsf(apq) > 1e-30f * (fabsf(app) + fabsf(aqq)) && apq != 0.f) ? t : 0.f;
-                t = isfinite(t) ? t : 0.f;
-                const float c = rsqrtf(fmaf(t, t, 1.f));
-                const float sn = t * c;
-                a[sym_idx(p, p)] = app - t * apq;
-                a[sym_idx(q, q)] = aqq + t * apq;
-                a[sym_idx(p, q)] = 0.f;
-#pragma unroll
-                for (int r = 0; r < 6; ++r) {
-                    if (r == p || r == q) continue;
-                    const float arp = a[sym_idx(r, p)], arq = a[sym_idx(r, q)];
-                    a[sym_idx(r, p)] = c * arp - sn * arq;
-                    a[sym_idx(r, q)] = sn * arp + c * arq;
-                }
-#pragma unroll
-                for (int r = 0; r < 6; ++r) {
-                    const float vp = V[r][p], vq = V[r][q];
-                    V[r][p] = c * vp - sn * vq;
-                    V[r][q] = sn * vp + c * vq;
-                }
-            }
+        jacobi_round<0, 1, 2, 3, 4, 5>(a, V);
+        jacobi_round<0, 2, 1, 4, 3, 5>(a, V);
+        jacobi_round<0, 3, 1, 5, 2, 4>(a, V);
+        jacobi_round<0, 4, 1, 3, 2, 5>(a, V);
+        jacobi_round<0, 5, 1, 2, 3, 4>(a, V);
     }
-    // pick the smallest diagonal
-    float best = a[sym_idx(0, 0)];
+    float best = a[0][0];
     float x[6];
 #pragma unroll
     for (int r = 0; r < 6; ++r) x[r] = V[r][0];
 #pragma unroll
     for (int c = 1; c < 6; ++c) {
-        const float d = a[sym_idx(c, c)];
+        const float d = a[c][c];
         const bool take = d < best;
         best = take ? d : best;
 #pragma unroll
         for (int r = 0; r < 6; ++r) x[r] = take ? V[r][c] : x[r];
     }
-    // double-precision Rayleigh quotient
     double xd[6], num = 0.0, den = 0.0;
 #pragma unroll
     for (int r = 0; r < 6; ++r) xd[r] = (double)x[r];

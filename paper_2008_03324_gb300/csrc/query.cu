@@ -64,325 +64,394 @@ __device__ __forceinline__ int mom_slot(int e, int j) {
     return -1;
 }
 
-// Assemble T = sum_j w_j M_dj^T S_j M_dj (reference point: the base node c0) from the
-// superset sums.  With X_j = -[d_j]x = -res sum_a b_a(j) K_a:
-//   T_TT = A^0
-//   T_TR = B^0 - res sum_a A^a K_a
-//   T_RR = D^0 - res sum_a (K_a^T B^a + B^a^T K_a) + res^2 sum_{a,c} K_a^T A^{ac} K_c
-// (A^{aa} = A^a since b_a^2 = b_a).
-__device__ __forceinline__ void assemble_T(const float* mom, float res, Blocks& T) {
-    // A^m packed as (0,0) (0,1) (0,2) (1,1) (1,2) (2,2)
-    auto Am = [&](int m, int r, int c) { return mom[m * 6 + sym3_idx(r, c)]; };
-    auto Bm = [&](int ms, int r, int c) { return mom[42 + ms * 9 + r * 3 + c]; };
-    auto Dm = [&](int r, int c) { return mom[78 + sym3_idx(r, c)]; };
-    const int jsingle[3] = {1, 2, 4};
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            T.A[r][c] = Am(0, r, c);
-            // TR
-            float v = Bm(0, r, c);
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                float acc = 0.f;
-#pragma unroll
-                for (int l = 0; l < 3; ++l) acc += Am(jsingle[a], r, l) * kx(a, l, c);
-                v -= res * acc;
-            }
-            T.B[r][c] = v;
-        }
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            float v = Dm(r, c);
-            float lin = 0.f;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const int ms = a + 1;  // B superset slot of the single bit a
-#pragma unroll
-                for (int l = 0; l < 3; ++l) lin += kx(a, l, r) * Bm(ms, l, c) + Bm(ms, l, r) * kx(a, l, c);
-            }
-            float quad = 0.f;
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-#pragma unroll
-                for (int b = 0; b < 3; ++b) {
-                    const int m = jsingle[a] | jsingle[b];
-#pragma unroll
-                    for (int l = 0; l < 3; ++l)
-#pragma unroll
-                        for (int n = 0; n < 3; ++n) quad += kx(a, l, r) * Am(m, l, n) * kx(b, n, c);
-                }
-            T.D[r][c] = v - res * lin + res * res * quad;
-        }
+// ---- warp-specialised kernel ----------------------------------------------------------
+// kGather gather warps stream corners and assemble T; kMetric metric warps finish poses.
+// Metric warp m serves gather warps m and m + kMetric (two slots each, double-buffered).
+constexpr int kGather = 6;     // default number of gather warps per CTA
+constexpr int kMetric = 3;     // default number of metric warps per CTA
+constexpr int kRow = 33;              // floats per pose in a slot (odd stride: no bank conflicts)
+// slot row: [0..20] T (about the base node, world axes), [21..23] t, [24..27] q,
+//           [28..30] c0, [31] status bits
+constexpr int kSlotFloats = 32 * kRow;
+
+template <int kElem, int NS>
+struct GatherSmem {
+    unsigned char stage[NS][Layout<kElem>::kPoseBytes];
+    PoseEntry ptab[32];
+    float mom[kMomStride];
+    float slot[2][kSlotFloats];
+    uint64_t bars[NS];
+    uint64_t full[2];
+    uint64_t empty[2];
+};
+
+template <int kElem, int NS>
+constexpr int gather_smem_bytes() {
+    return (int)((sizeof(GatherSmem<kElem, NS>) + 127) / 128 * 128);
 }
 
-template <int kElem>
-constexpr int warp_bytes() {
-    return ((kStages * Layout<kElem>::kPoseBytes + 32 * (int)sizeof(PoseEntry) + 32 * kMomStride * 4 + 64 + 127) / 128) * 128;
+// Entry e of T as a linear combination of the 84 superset sums,
+//   T[e] = sum_{u < 9} coef_u(res) * mom[idx_u]   (unused terms have coef 0),
+// following the algebra of the reference-point change:
+//   T_TT = A^0,  T_TR = B^0 - res sum_a A^a K_a,
+//   T_RR = D^0 - res (L + L^T) + res^2 Q,  L = sum_a K_a^T B^a,  Q = sum_ab K_a^T A^{ab} K_b,
+// K_a = [e_a]x, A^{ab} the superset sum of corners with bits a and b set (A^{aa} = A^a).
+// t_term returns term number u (the enumeration order is fixed); called once per lane.
+__device__ void t_term(int e, float res, int u, int& idx_out, float& coef_out) {
+    int n = 0;
+    idx_out = 0;
+    coef_out = 0.f;
+    auto add = [&](int idx, float c) {
+        if (c == 0.f) return;
+        if (n == u) { idx_out = idx; coef_out = c; }
+        ++n;
+    };
+    auto A = [&](int m, int r, int c) { return m * 6 + sym3_idx(r, c); };
+    auto B = [&](int ms, int r, int c) { return 42 + ms * 9 + r * 3 + c; };
+    auto D = [&](int r, int c) { return 78 + sym3_idx(r, c); };
+    const int R = sym_row(e), C = sym_col(e);
+    if (R < 3 && C < 3) {
+        add(A(0, R, C), 1.f);
+    } else if (R < 3) {
+        const int r = R, c = C - 3;
+        add(B(0, r, c), 1.f);
+        for (int a = 0; a < 3; ++a)
+            for (int l = 0; l < 3; ++l) add(A(1 << a, r, l), -res * kx(a, l, c));
+    } else {
+        const int r = R - 3, c = C - 3;
+        add(D(r, c), 1.f);
+        for (int a = 0; a < 3; ++a)
+            for (int l = 0; l < 3; ++l) {
+                add(B(a + 1, l, c), -res * kx(a, l, r));
+                add(B(a + 1, l, r), -res * kx(a, l, c));
+            }
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                for (int l = 0; l < 3; ++l)
+                    for (int m = 0; m < 3; ++m) add(A((1 << a) | (1 << b), l, m), res * res * kx(a, l, r) * kx(b, m, c));
+    }
 }
 
-template <int kElem>
-__global__ void __launch_bounds__(kWarps * 32) query_kernel(QueryArgs args) {
+// NG gather warps, NM metric warps (NG a multiple of NM), NS pose stages per gather warp,
+// L2 prefetch NP poses beyond the stages
+template <int kElem, int NG, int NM, int NS, int NP>
+__global__ void __launch_bounds__((NG + NM) * 32, 1) query_kernel(QueryArgs args) {
     using L = Layout<kElem>;
+    using GS = GatherSmem<kElem, NS>;
+    constexpr int kStages = NS;
+    constexpr int kPrefetch = NP;
+    constexpr int kGather = NG;
+    constexpr int kMetric = NM;
+    static_assert(NG % NM == 0, "each metric warp serves the same number of gather warps");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    // per-warp shared memory (each warp's region starts on a 128-B boundary)
-    constexpr int kWarpBytes = warp_bytes<kElem>();
-    unsigned char* wbase = smem_raw + warp * kWarpBytes;
-    unsigned char* stage = wbase;
-    PoseEntry* ptab = reinterpret_cast<PoseEntry*>(wbase + kStages * L::kPoseBytes);
-    float* mom = reinterpret_cast<float*>(wbase + kStages * L::kPoseBytes + 32 * sizeof(PoseEntry));
-    uint64_t* bars = reinterpret_cast<uint64_t*>(wbase + kStages * L::kPoseBytes + 32 * sizeof(PoseEntry) +
-                                                 32 * kMomStride * 4);
+    constexpr int kGB = gather_smem_bytes<kElem, NS>();
+    const int64_t groups = (args.m + 31) / 32;
+    const int64_t ngather = (int64_t)gridDim.x * kGather;
 
-    if (lane == 0) {
-#pragma unroll
-        for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 4);
+    if (threadIdx.x < kGather) {
+        GS& G = *reinterpret_cast<GS*>(smem_raw + threadIdx.x * kGB);
+        for (int s = 0; s < kStages; ++s) mbar_init(&G.bars[s], 4);
+        for (int s = 0; s < 2; ++s) { mbar_init(&G.full[s], 1); mbar_init(&G.empty[s], 1); }
         fence_mbar_init();
     }
-    __syncwarp();
+    __syncthreads();
 
-    const int j = lane >> 2;  // corner: bits (x, y, z)
-    const int q = lane & 3;   // entry quarter
-    const int bx = j & 1, by = (j >> 1) & 1, bz = (j >> 2) & 1;
-    const int P = j >> 1;     // node pair holding this corner
-    int slot[6];
+    if (warp < kGather) {
+        // =============================== gather warp ===============================
+        GS& G = *reinterpret_cast<GS*>(smem_raw + warp * kGB);
+        const int j = lane >> 2, q = lane & 3;
+        const int bx = j & 1, by = (j >> 1) & 1, bz = (j >> 2) & 1;
+        int mslot[6];
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
-        const int e = q + 4 * i;
-        slot[i] = (e < 21) ? mom_slot(e, j) : -1;
-    }
-    const int corner_off = L::slot(P) + bx * L::kNodeBytes;  // byte offset of my corner in a stage
-
-    const int64_t nx = args.nx, nxy = (int64_t)args.nx * args.ny;
-    const char* coeffs = reinterpret_cast<const char*>(args.coeffs);
-    uint32_t phase_bits = 0;     // parity of the next wait, per stage
-    bool ok = true;
-
-    const int64_t groups = (args.m + 31) / 32;
-    const int64_t gwarp = (int64_t)blockIdx.x * kWarps + warp;
-    const int64_t nwarps = (int64_t)gridDim.x * kWarps;
-
-    auto pair_src = [&](int64_t base, int pp) -> const void* {
-        const int64_t node = base + (pp & 1) * nx + (pp >> 1) * nxy;
-        return coeffs + node * (int64_t)L::kNodeBytes;
-    };
-
-    for (int64_t g = gwarp; g < groups; g += nwarps) {
-        const int64_t p0 = g * 32;
-        const int cnt = (int)(int)(args.m - p0 < 32 ? args.m - p0 : 32);
-        // ---------------- phase P: lane = pose ----------------
-        float t[3] = {0.f, 0.f, 0.f}, qv[4] = {1.f, 0.f, 0.f, 0.f};
-        int i0[3] = {0, 0, 0};
-        uint32_t st = 0;
-        if (lane < cnt) {
-            const float* ps = args.poses + (p0 + lane) * 7;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) t[a] = __ldg(ps + a);
-#pragma unroll
-            for (int a = 0; a < 4; ++a) qv[a] = __ldg(ps + 3 + a);
-            bool finite = true;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) finite &= isfinite(t[a]);
-#pragma unroll
-            for (int a = 0; a < 4; ++a) finite &= isfinite(qv[a]);
-            float R[3][3];
-            const float n2 = quat_to_rot(qv[0], qv[1], qv[2], qv[3], R);
-            finite &= (n2 > 0.f) && isfinite(n2);
-            if (!finite) st |= FIF_POSE_NAN;
-            if (fabsf(n2 - 1.f) > 1e-3f) st |= FIF_POSE_QUAT;
-            float w[3];
-            const float org[3] = {args.ox, args.oy, args.oz};
-            const int dims[3] = {args.nx, args.ny, args.nz};
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                float gg = __fdiv_rn(__fsub_rn(t[a], org[a]), args.res);
-                if (!(st & FIF_POSE_NAN)) {
-                    if (gg < 0.f || gg > (float)(dims[a] - 1)) st |= FIF_POSE_OUTSIDE;
-                } else {
-                    gg = 0.f;
-                }
-                if (args.flags & FIF_Q_NEAREST) {
-                    int ii = (int)floorf(__fadd_rn(gg, 0.5f));
-                    ii = max(0, min(ii, dims[a] - 1));
-                    const int b0 = min(ii, dims[a] - 2);
-                    i0[a] = b0;
-                    w[a] = (ii > b0) ? 1.f : 0.f;
-                } else {
-                    int ii = (int)floorf(gg);
-                    ii = max(0, min(ii, dims[a] - 2));
-                    i0[a] = ii;
-                    w[a] = fminf(fmaxf(gg - (float)ii, 0.f), 1.f);
-                }
-            }
-            const float z[3] = {R[0][2], R[1][2], R[2][2]};
-            float vr[10];
-            vis_vr(z, args.k0, args.k1, args.k2, vr);
-            if (st & FIF_POSE_NAN) {
-#pragma unroll
-                for (int k = 0; k < 10; ++k) vr[k] = 0.f;
-            }
-            const int64_t base = i0[0] + nx * i0[1] + nxy * i0[2];
-            PoseEntry& pe = ptab[lane];
-            pe.base_lo = (int32_t)(base & 0xffffffff);
-            pe.base_hi = (int32_t)(base >> 32);
-            pe.w[0] = w[0]; pe.w[1] = w[1]; pe.w[2] = w[2];
-#pragma unroll
-            for (int k = 0; k < 10; ++k) pe.vr[k] = vr[k];
-            pe.status = st;
+        for (int ii = 0; ii < 6; ++ii) {
+            const int e = q + 4 * ii;
+            mslot[ii] = (e < 21) ? mom_slot(e, j) : -1;
         }
-        __syncwarp();
-        auto base_of = [&](int i) -> int64_t {
-            return (int64_t)(uint32_t)ptab[i].base_lo | ((int64_t)ptab[i].base_hi << 32);
+        const int corner_off = L::slot(j >> 1) + bx * L::kNodeBytes;
+        int t_idx[9];
+        float t_coef[9];
+#pragma unroll
+        for (int u = 0; u < 9; ++u) t_term(lane < 21 ? lane : 0, args.res, u, t_idx[u], t_coef[u]);
+        const int64_t nx = args.nx, nxy = (int64_t)args.nx * args.ny;
+        const char* coeffs = reinterpret_cast<const char*>(args.coeffs);
+        auto pair_src = [&](int64_t base, int pp) -> const void* {
+            return coeffs + (base + (pp & 1) * nx + (pp >> 1) * nxy) * (int64_t)L::kNodeBytes;
         };
-        // prologue: L2 prefetch of the first poses, bulk copies of the first stages
-        if (lane < 4) {
-            for (int i = 0; i < min(cnt, kPrefetch + kStages - 1); ++i)
-                bulk_prefetch_l2(pair_src(base_of(i), lane), L::kPairBytes);
-            fence_proxy_async();
-            for (int i = 0; i < min(cnt, kStages - 1); ++i) {
-                uint64_t* bar = &bars[i % kStages];
-                unsigned char* dst = stage + (i % kStages) * L::kPoseBytes + L::slot(lane);
-                mbar_arrive_expect_tx(bar, L::kPairBytes);
-                bulk_g2s(dst, pair_src(base_of(i), lane), L::kPairBytes, bar);
-            }
-        }
-        // ---------------- phase G: warp per pose ----------------
-        for (int i = 0; i < cnt; ++i) {
-            const int s = i % kStages;
-            if (lane < 4) {
-                const int inext = i + kStages - 1;
-                if (inext < cnt) {
-                    const int sn = inext % kStages;
-                    fence_proxy_async();
-                    uint64_t* bar = &bars[sn];
-                    mbar_arrive_expect_tx(bar, L::kPairBytes);
-                    bulk_g2s(stage + sn * L::kPoseBytes + L::slot(lane), pair_src(base_of(inext), lane),
-                             L::kPairBytes, bar);
+        uint32_t phase_bits = 0;
+        int k = 0;
+        for (int64_t g = (int64_t)blockIdx.x * kGather + warp; g < groups; g += ngather, ++k) {
+            const int sl = k & 1;
+            const uint32_t use = (uint32_t)(k >> 1);
+            if (!mbar_wait_bounded(&G.empty[sl], (use & 1u) ^ 1u)) set_error(args.err, FIF_ETIMEOUT);
+            float* slot = G.slot[sl];
+            const int64_t p0 = g * 32;
+            const int cnt = (int)(args.m - p0 < 32 ? args.m - p0 : 32);
+            // ---- phase P: lane = pose ----
+            if (lane < cnt) {
+                const float* ps = args.poses + (p0 + lane) * 7;
+                float t[3], qv[4];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) t[a] = __ldg(ps + a);
+#pragma unroll
+                for (int a = 0; a < 4; ++a) qv[a] = __ldg(ps + 3 + a);
+                uint32_t st = 0;
+                bool finite = true;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) finite &= isfinite(t[a]);
+#pragma unroll
+                for (int a = 0; a < 4; ++a) finite &= isfinite(qv[a]);
+                float R[3][3];
+                const float n2 = quat_to_rot(qv[0], qv[1], qv[2], qv[3], R);
+                finite &= (n2 > 0.f) && isfinite(n2);
+                if (!finite) st |= FIF_POSE_NAN;
+                if (fabsf(n2 - 1.f) > 1e-3f) st |= FIF_POSE_QUAT;
+                const float org[3] = {args.ox, args.oy, args.oz};
+                const int dims[3] = {args.nx, args.ny, args.nz};
+                float w[3];
+                int i0[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    float gg = __fdiv_rn(__fsub_rn(t[a], org[a]), args.res);
+                    if (!(st & FIF_POSE_NAN)) {
+                        if (gg < 0.f || gg > (float)(dims[a] - 1)) st |= FIF_POSE_OUTSIDE;
+                    } else {
+                        gg = 0.f;
+                    }
+                    if (args.flags & FIF_Q_NEAREST) {
+                        int ii = (int)floorf(__fadd_rn(gg, 0.5f));
+                        ii = max(0, min(ii, dims[a] - 1));
+                        const int b0 = min(ii, dims[a] - 2);
+                        i0[a] = b0;
+                        w[a] = (ii > b0) ? 1.f : 0.f;
+                    } else {
+                        int ii = (int)floorf(gg);
+                        ii = max(0, min(ii, dims[a] - 2));
+                        i0[a] = ii;
+                        w[a] = fminf(fmaxf(gg - (float)ii, 0.f), 1.f);
+                    }
                 }
-                const int ipf = i + kStages - 1 + kPrefetch;
-                if (ipf < cnt) bulk_prefetch_l2(pair_src(base_of(ipf), lane), L::kPairBytes);
+                const float z[3] = {R[0][2], R[1][2], R[2][2]};
+                float vr[10];
+                vis_vr(z, args.k0, args.k1, args.k2, vr);
+                if (st & FIF_POSE_NAN) {
+#pragma unroll
+                    for (int kk = 0; kk < 10; ++kk) vr[kk] = 0.f;
+                }
+                const int64_t base = i0[0] + nx * i0[1] + nxy * i0[2];
+                PoseEntry& pe = G.ptab[lane];
+                pe.base_lo = (int32_t)(base & 0xffffffff);
+                pe.base_hi = (int32_t)(base >> 32);
+                pe.w[0] = w[0]; pe.w[1] = w[1]; pe.w[2] = w[2];
+#pragma unroll
+                for (int kk = 0; kk < 10; ++kk) pe.vr[kk] = vr[kk];
+                pe.status = st;
+                float* row = slot + lane * kRow;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) row[21 + a] = t[a];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) row[24 + a] = qv[a];
+                row[28] = __fadd_rn(args.ox, __fmul_rn(args.res, (float)i0[0]));
+                row[29] = __fadd_rn(args.oy, __fmul_rn(args.res, (float)i0[1]));
+                row[30] = __fadd_rn(args.oz, __fmul_rn(args.res, (float)i0[2]));
+                row[31] = __uint_as_float(st);
             }
-            const uint32_t par = (phase_bits >> s) & 1u;
-            if (!mbar_wait_bounded(&bars[s], par)) {
-                ok = false;
-                set_error(args.err, FIF_ETIMEOUT);
+            __syncwarp();
+            auto base_of = [&](int i) -> int64_t {
+                return (int64_t)(uint32_t)G.ptab[i].base_lo | ((int64_t)G.ptab[i].base_hi << 32);
+            };
+            if (lane < 4) {
+                for (int i = 0; i < min(cnt, kPrefetch + kStages - 1); ++i)
+                    bulk_prefetch_l2(pair_src(base_of(i), lane), L::kPairBytes);
+                fence_proxy_async();
+                for (int i = 0; i < min(cnt, kStages - 1); ++i) {
+                    uint64_t* bar = &G.bars[i % kStages];
+                    mbar_arrive_expect_tx(bar, L::kPairBytes);
+                    bulk_g2s(G.stage[i % kStages] + L::slot(lane), pair_src(base_of(i), lane), L::kPairBytes, bar);
+                }
             }
-            phase_bits ^= (1u << s);
-            // corner weight and weighted v_r
-            const PoseEntry& pe = ptab[i];
-            const float wj = (bx ? pe.w[0] : 1.f - pe.w[0]) * (by ? pe.w[1] : 1.f - pe.w[1]) *
-                             (bz ? pe.w[2] : 1.f - pe.w[2]);
-            float vrj[10];
+            // ---- phase G: warp per pose ----
+            for (int i = 0; i < cnt; ++i) {
+                const int s = i % kStages;
+                if (lane < 4) {
+                    const int inext = i + kStages - 1;
+                    if (inext < cnt) {
+                        const int sn = inext % kStages;
+                        fence_proxy_async();
+                        mbar_arrive_expect_tx(&G.bars[sn], L::kPairBytes);
+                        bulk_g2s(G.stage[sn] + L::slot(lane), pair_src(base_of(inext), lane), L::kPairBytes,
+                                 &G.bars[sn]);
+                    }
+                    const int ipf = i + kStages - 1 + kPrefetch;
+                    if (ipf < cnt) bulk_prefetch_l2(pair_src(base_of(ipf), lane), L::kPairBytes);
+                }
+                if (!mbar_wait_bounded(&G.bars[s], (phase_bits >> s) & 1u)) set_error(args.err, FIF_ETIMEOUT);
+                phase_bits ^= (1u << s);
+                const PoseEntry& pe = G.ptab[i];
+                const float wj = (bx ? pe.w[0] : 1.f - pe.w[0]) * (by ? pe.w[1] : 1.f - pe.w[1]) *
+                                 (bz ? pe.w[2] : 1.f - pe.w[2]);
+                float vrj[10];
 #pragma unroll
-            for (int k = 0; k < 10; ++k) vrj[k] = wj * pe.vr[k];
-            const float* C = reinterpret_cast<const float*>(stage + s * L::kPoseBytes + corner_off) + q;
-            float v[6];
-#pragma unroll
-            for (int ii = 0; ii < 6; ++ii) {
-                float acc = 0.f;
-#pragma unroll
-                for (int k = 0; k < 10; ++k) acc = fmaf(vrj[k], C[k * 21 + 4 * ii], acc);
-                v[ii] = acc;
-            }
-            // superset-sum butterfly over the corner bits x (lane bit 2), y (3), z (4)
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const int mask = 4 << a;
-                const bool low = ((j >> a) & 1) == 0;
+                for (int kk = 0; kk < 10; ++kk) vrj[kk] = wj * pe.vr[kk];
+                const float* C = reinterpret_cast<const float*>(G.stage[s] + corner_off) + q;
+                float v[6];
 #pragma unroll
                 for (int ii = 0; ii < 6; ++ii) {
-                    const float o = __shfl_xor_sync(0xffffffffu, v[ii], mask);
-                    v[ii] = low ? v[ii] + o : v[ii];
-                }
-            }
-            float* mrow = mom + i * kMomStride;
+                    float acc = 0.f;
 #pragma unroll
-            for (int ii = 0; ii < 6; ++ii)
-                if (slot[ii] >= 0) mrow[slot[ii]] = v[ii];
-            __syncwarp();
+                    for (int kk = 0; kk < 10; ++kk) acc = fmaf(vrj[kk], C[kk * 21 + 4 * ii], acc);
+                    v[ii] = acc;
+                }
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const int mask = 4 << a;
+                    const bool low = ((j >> a) & 1) == 0;
+#pragma unroll
+                    for (int ii = 0; ii < 6; ++ii) {
+                        const float o = __shfl_xor_sync(0xffffffffu, v[ii], mask);
+                        v[ii] = low ? v[ii] + o : v[ii];
+                    }
+                }
+#pragma unroll
+                for (int ii = 0; ii < 6; ++ii)
+                    if (mslot[ii] >= 0) G.mom[mslot[ii]] = v[ii];
+                __syncwarp();
+                if (lane < 21) {
+                    float acc = 0.f;
+#pragma unroll
+                    for (int u = 0; u < 9; ++u) acc = fmaf(t_coef[u], G.mom[t_idx[u]], acc);
+                    slot[i * kRow + lane] = acc;
+                }
+                __syncwarp();
+            }
+            fence_proxy_async();
+            if (lane == 0) mbar_arrive(&G.full[sl]);
         }
-        // ---------------- phase F: lane = pose ----------------
-        if (lane < cnt) {
-            const PoseEntry& pe = ptab[lane];
-            st = pe.status;
-            Blocks T;
-            assemble_T(mom + lane * kMomStride, args.res, T);
-            const float c0[3] = {__fadd_rn(args.ox, __fmul_rn(args.res, (float)i0[0])),
-                                 __fadd_rn(args.oy, __fmul_rn(args.res, (float)i0[1])),
-                                 __fadd_rn(args.oz, __fmul_rn(args.res, (float)i0[2]))};
-            float fim[21];
-            if (args.flags & FIF_Q_WORLD) {
-                shift_ref(T, c0);
-            } else {
-                float R[3][3];
-                quat_to_rot(qv[0], qv[1], qv[2], qv[3], R);
-                // the coefficients were taken at the clamped cell; the FIM is expressed about t
-                const float b[3] = {c0[0] - t[0], c0[1] - t[1], c0[2] - t[2]};
-                shift_ref(T, b);
-                rotate_into(T, R);
-            }
-            pack(T, fim);
-            const bool nan = (st & FIF_POSE_NAN) != 0;
-            if (nan) {
+    } else {
+        // =============================== metric warp ===============================
+        const int mw = warp - kGather;
+        int k = 0;
+        for (;; ++k) {
+            bool any = false;
+#pragma unroll 1
+            for (int h = 0; h < kGather / kMetric; ++h) {
+                const int gw = mw + h * kMetric;
+                const int64_t g = (int64_t)blockIdx.x * kGather + gw + (int64_t)k * ngather;
+                if (g >= groups) continue;
+                any = true;
+                GS& G = *reinterpret_cast<GS*>(smem_raw + gw * kGB);
+                const int sl = k & 1;
+                const uint32_t use = (uint32_t)(k >> 1);
+                if (!mbar_wait_bounded(&G.full[sl], use & 1u)) set_error(args.err, FIF_ETIMEOUT);
+                const float* slot = G.slot[sl];
+                const int64_t p0 = g * 32;
+                const int cnt = (int)(args.m - p0 < 32 ? args.m - p0 : 32);
+                if (lane < cnt) {
+                    const float* row = slot + lane * kRow;
+                    float Tp[21];
 #pragma unroll
-                for (int e = 0; e < 21; ++e) fim[e] = __int_as_float(0x7fc00000);
-            }
-            const int64_t pid = p0 + lane;
-            if (args.fim) {
-                float* out = args.fim + pid * 21;
+                    for (int e = 0; e < 21; ++e) Tp[e] = row[e];
+                    const float t[3] = {row[21], row[22], row[23]};
+                    const float c0[3] = {row[28], row[29], row[30]};
+                    uint32_t st = __float_as_uint(row[31]);
+                    Blocks T;
+                    unpack(Tp, T);
+                    if (args.flags & FIF_Q_WORLD) {
+                        shift_ref(T, c0);
+                    } else {
+                        float R[3][3];
+                        quat_to_rot(row[24], row[25], row[26], row[27], R);
+                        const float b[3] = {c0[0] - t[0], c0[1] - t[1], c0[2] - t[2]};
+                        shift_ref(T, b);
+                        rotate_into(T, R);
+                    }
+                    float fim[21];
+                    pack(T, fim);
+                    const bool nan = (st & FIF_POSE_NAN) != 0;
+                    if (nan) {
 #pragma unroll
-                for (int e = 0; e < 21; ++e) out[e] = fim[e];
+                        for (int e = 0; e < 21; ++e) fim[e] = __int_as_float(0x7fc00000);
+                    }
+                    const int64_t pid = p0 + lane;
+                    // stage the outputs in this pose's slot row (T, t and q are consumed) so the
+                    // warp can write them out with coalesced stores
+                    float* wrow = const_cast<float*>(row);
+#pragma unroll
+                    for (int e = 0; e < 21; ++e) wrow[e] = fim[e];
+                    double mv[3] = {0.0, 0.0, 0.0};
+                    if (args.flags & FIF_Q_METRICS) {
+                        if (args.flags & FIF_Q_TRACE) mv[0] = nan ? (double)NAN : (double)trace6(fim);
+                        if (args.flags & FIF_Q_LOGDET) {
+                            double lad;
+                            int sg;
+                            logdet_f64(fim, lad, sg);
+                            if (nan) { lad = NAN; sg = 0; }
+                            mv[1] = lad;
+                            if (args.sign) args.sign[pid] = (int8_t)sg;
+                            if (sg <= 0 && !nan) st |= FIF_POSE_NOT_PD;
+                        }
+                        if (args.flags & FIF_Q_LMIN) {
+                            double lm = lambda_min_f64(fim);
+                            if (nan) lm = NAN;
+                            mv[2] = lm;
+                            if (!(lm > 0.0) && !nan) st |= FIF_POSE_NOT_PD;
+                        }
+                    }
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const unsigned long long b = (unsigned long long)__double_as_longlong(mv[c]);
+                        wrow[21 + 2 * c] = __uint_as_float((uint32_t)(b & 0xffffffffu));
+                        wrow[22 + 2 * c] = __uint_as_float((uint32_t)(b >> 32));
+                    }
+                    if (args.status) args.status[pid] = (int32_t)st;
+                }
+                __syncwarp();
+                if (args.fim) {
+                    float* out = args.fim + p0 * 21;
+                    for (int idx = lane; idx < cnt * 21; idx += 32) out[idx] = slot[(idx / 21) * kRow + idx % 21];
+                }
+                if (args.metrics && (args.flags & FIF_Q_METRICS)) {
+                    const int cols = args.flags & FIF_Q_METRICS;
+                    double* out = args.metrics + p0 * 3;
+                    for (int idx = lane; idx < cnt * 3; idx += 32) {
+                        const int c = idx % 3;
+                        if (!(cols & (FIF_Q_TRACE << c))) continue;   // unselected columns stay untouched
+                        const float* r = slot + (idx / 3) * kRow + 21 + 2 * c;
+                        const unsigned long long b =
+                            (unsigned long long)__float_as_uint(r[0]) | ((unsigned long long)__float_as_uint(r[1]) << 32);
+                        out[idx] = __longlong_as_double((long long)b);
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&G.empty[sl]);
             }
-            if (args.flags & FIF_Q_METRICS) {
-                double* mo = args.metrics ? args.metrics + pid * 3 : nullptr;
-                if (args.flags & FIF_Q_TRACE) {
-                    if (mo) mo[0] = nan ? (double)NAN : (double)trace6(fim);
-                }
-                if (args.flags & FIF_Q_LOGDET) {
-                    double lad;
-                    int sg;
-                    logdet_f64(fim, lad, sg);
-                    if (nan) { lad = NAN; sg = 0; }
-                    if (mo) mo[1] = lad;
-                    if (args.sign) args.sign[pid] = (int8_t)sg;
-                    if (sg <= 0 && !nan) st |= FIF_POSE_NOT_PD;
-                }
-                if (args.flags & FIF_Q_LMIN) {
-                    double lm = lambda_min_f64(fim);
-                    if (nan) lm = NAN;
-                    if (mo) mo[2] = lm;
-                    if (!(lm > 0.0) && !nan) st |= FIF_POSE_NOT_PD;
-                }
-            }
-            if (args.status) args.status[pid] = (int32_t)st;
+            if (!any) break;
         }
-        __syncwarp();
     }
-    (void)ok;
 }
 
 }  // namespace
 
-int launch_query(const QueryArgs& a, cudaStream_t stream) {
-    const int smem = kWarps * warp_bytes<4>();
-    if (cudaFuncSetAttribute(query_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+template <int NG, int NM, int NS, int NP>
+int launch_query_cfg(const QueryArgs& a, cudaStream_t stream) {
+    auto kern = query_kernel<4, NG, NM, NS, NP>;
+    const int smem = NG * gather_smem_bytes<4, NS>();
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return FIF_ECUDA;
-    int dev = 0, sms = 0, per_sm = 0;
+    int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, query_kernel<4>, kWarps * 32, smem);
-    if (per_sm < 1) per_sm = 1;
     const int64_t groups = (a.m + 31) / 32;
-    const int64_t need = (groups + kWarps - 1) / kWarps;
-    const int64_t grid = std::min<int64_t>(need, (int64_t)sms * per_sm);
+    const int64_t need = (groups + NG - 1) / NG;
+    const int64_t grid = std::min<int64_t>(need, (int64_t)sms);
     if (grid <= 0) return FIF_OK;
-    query_kernel<4><<<(unsigned)grid, kWarps * 32, smem, stream>>>(a);
+    kern<<<(unsigned)grid, (NG + NM) * 32, smem, stream>>>(a);
     return cudaPeekAtLastError() == cudaSuccess ? FIF_OK : FIF_ECUDA;
+}
+
+int launch_query(const QueryArgs& a, cudaStream_t stream) {
+    return launch_query_cfg<kGather, kMetric, kStages, kPrefetch>(a, stream);
 }
 
 }  // namespace fif
