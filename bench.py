@@ -356,6 +356,36 @@ def main():
     out["pointcloud"] = {"queries_per_s": pc_rate, "landmarks": int(lm.shape[0]), "poses": mp,
                          "field_speedup": (value / ws) / pc_rate}
 
+    # ---------------- bfloat16 storage (same map, same poses) ----------------
+    field16 = fif.Field(spec.origin, spec.res, spec.dims, params, storage=fif.STORAGE_BF16)
+    fif.build(field16.c, lm, wsb)
+    t16 = time_events(lambda: fif.query(field16.c, poses, fif.Q_METRICS, fim, met, sg, st), 10, 3, stream)
+    ms16 = float(np.mean(t16))
+    b16 = 8 * 210 * 2 + 7 * 4 + 21 * 4 + 3 * 8 + 1 + 4
+    out["bf16"] = {"queries_per_s": m / (ms16 * 1e-3), "kernel_ms": ms16, "bytes_per_pose": b16,
+                   "roofline": {"bound": "hbm", "achieved": m * b16 / (ms16 * 1e-3) / 1e9, "peak": hbm_peak,
+                                "unit": "GB/s", "frac": m * b16 / (ms16 * 1e-3) / 1e9 / hbm_peak}}
+    del field16
+    torch.cuda.empty_cache()
+
+    # ---------------- differentiable trajectory batch (256 x 128 samples) ----------------
+    from paper_2008_03324_gb300 import traj
+    ctrl_np, yaw_np, basis_np = synth.bspline_batch(6, scene, 256, 32, 128)
+    field08 = field.with_params(fif.make_params(r_max=r_max, v_alpha=0.8))
+    B_t = torch.from_numpy(basis_np.astype(np.float32)).to(dev)
+    yaw_t = torch.from_numpy(yaw_np.astype(np.float32)).to(dev)
+    ctrl_t = torch.from_numpy(ctrl_np.astype(np.float32)).to(dev).requires_grad_(True)
+
+    def traj_step():
+        ctrl_t.grad = None
+        loss, phi, tm, tsg = traj.neg_logdet_objective(ctrl_t, yaw_t, B_t, field08)
+        loss.backward()
+
+    ttj = time_events(traj_step, 10, 3, stream)
+    out["trajopt"] = {"trajectories": 256, "samples": 128, "poses": 256 * 128, "v_alpha": 0.8,
+                      "ms_forward_backward": float(np.mean(ttj)),
+                      "poses_per_s": 256 * 128 / (float(np.mean(ttj)) * 1e-3)}
+
     # ---------------- serving (rank 0) ----------------
     if rank == 0 and args.serve_requests > 0:
         reqs = synth.request_stream(3, args.serve_requests, scene)

@@ -186,6 +186,7 @@ struct BuildSmem {
     float4 tile[kSlots][kTile];
     int2 runs[kMaxRuns];
     int tile_count[kSlots];
+    uint16_t keep[kThreads / 32][kTile];   // per-warp list of the tile's landmarks near its sub-brick
     int nruns;
     uint64_t bars[kSlots];
 };
@@ -241,7 +242,9 @@ __global__ void __launch_bounds__(kThreads, 2) build_kernel(BuildArgs a) {
     const int brick = blockIdx.x;
     const int bxi = brick % nbx, byi = (brick / nbx) % nby, bzi = brick / (nbx * nby);
     const int i0 = bxi * kBX, j0 = byi * kBY, k0 = bzi * kBZ;
-    const int ti = tid & 7, tj = (tid >> 3) & 3, tk = tid >> 5;
+    // warp w owns the 4 x 4 x 2 sub-brick at x offset 4 (w & 1), z offset 2 (w >> 1)
+    const int warp = tid >> 5, lane = tid & 31;
+    const int ti = 4 * (warp & 1) + (lane & 3), tj = (lane >> 2) & 3, tk = 2 * (warp >> 1) + (lane >> 4);
     const int ni = i0 + ti, nj = j0 + tj, nk = k0 + tk;
     const bool valid = ni < a.nx && nj < a.ny && nk < a.nz;
     const float cx = __fadd_rn(a.ox, __fmul_rn(a.res, (float)ni));
@@ -251,6 +254,13 @@ __global__ void __launch_bounds__(kThreads, 2) build_kernel(BuildArgs a) {
     const float blo[3] = {a.ox + a.res * i0, a.oy + a.res * j0, a.oz + a.res * k0};
     const float bhi[3] = {a.ox + a.res * min(i0 + kBX - 1, a.nx - 1), a.oy + a.res * min(j0 + kBY - 1, a.ny - 1),
                           a.oz + a.res * min(k0 + kBZ - 1, a.nz - 1)};
+
+    // this warp's sub-brick box (its valid nodes); a landmark farther than r_cull from it is
+    // outside every shell of the warp's nodes
+    const int wi0 = i0 + 4 * (warp & 1), wk0 = k0 + 2 * (warp >> 1);
+    const float wlo[3] = {a.ox + a.res * min(wi0, a.nx - 1), a.oy + a.res * j0, a.oz + a.res * min(wk0, a.nz - 1)};
+    const float whi[3] = {a.ox + a.res * min(wi0 + 3, a.nx - 1), a.oy + a.res * min(j0 + kBY - 1, a.ny - 1),
+                          a.oz + a.res * min(wk0 + 1, a.nz - 1)};
 
     for (int idx = tid; idx < kMom * kThreads; idx += kThreads) {
         (&S.hi[0][0])[idx] = 0.f;
@@ -361,13 +371,30 @@ __global__ void __launch_bounds__(kThreads, 2) build_kernel(BuildArgs a) {
         }
         const int cnt = S.tile_count[slot];
         if (cnt == 0) break;
-        cand += cnt;
         const float4* tile = S.tile[slot];
-        for (int b0 = 0; b0 < cnt; b0 += kBlock) {
-            const int b1 = min(cnt, b0 + kBlock);
+        // exact culling against this warp's sub-brick, compacted in tile order
+        uint16_t* keep = S.keep[warp];
+        int nkeep = 0;
+        for (int base = 0; base < cnt; base += 32) {
+            bool near = false;
+            if (base + lane < cnt) {
+                const float4 P = tile[base + lane];
+                const float ex = fmaxf(0.f, fmaxf(wlo[0] - P.x, P.x - whi[0]));
+                const float ey = fmaxf(0.f, fmaxf(wlo[1] - P.y, P.y - whi[1]));
+                const float ez = fmaxf(0.f, fmaxf(wlo[2] - P.z, P.z - whi[2]));
+                near = ex * ex + ey * ey + ez * ez <= rc2;
+            }
+            const unsigned mask = __ballot_sync(0xffffffffu, near);
+            if (near) keep[nkeep + __popc(mask & ((1u << lane) - 1u))] = (uint16_t)(base + lane);
+            nkeep += __popc(mask);
+        }
+        __syncwarp();
+        cand += nkeep;
+        for (int b0 = 0; b0 < nkeep; b0 += kBlock) {
+            const int b1 = min(nkeep, b0 + kBlock);
 #pragma unroll 2
             for (int l = b0; l < b1; ++l) {
-                const float4 L = tile[l];
+                const float4 L = tile[keep[l]];
                 const float dx = __fsub_rn(L.x, cx), dy = __fsub_rn(L.y, cy), dz = __fsub_rn(L.z, cz);
                 const float n2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
                 const bool in = (n2 > rmin2) && (n2 <= rmax2);
@@ -448,10 +475,8 @@ __global__ void __launch_bounds__(kThreads, 2) build_kernel(BuildArgs a) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if ((tid & 31) == 0 && v) atomicAdd(&stats[0], v);
-        if (tid == 0) {
-            int nvalid = (min(i0 + kBX, a.nx) - i0) * (min(j0 + kBY, a.ny) - j0) * (min(k0 + kBZ, a.nz) - k0);
-            atomicAdd(&stats[1], cand * (unsigned long long)nvalid);
-        }
+        const unsigned long long nv = __popc(__ballot_sync(0xffffffffu, valid));
+        if (lane == 0) atomicAdd(&stats[1], cand * nv);
     }
     if (!valid) return;
     // ---- epilogue: 66 moments -> 210 coefficients (times 1/sigma^2) ----

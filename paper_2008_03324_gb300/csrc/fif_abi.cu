@@ -203,7 +203,6 @@ int32_t fif_query(const fif_field* field, const float* d_poses, int64_t m, int32
     if (m < 0 || (m > 0 && !d_poses)) return FIF_EINVAL;
     if (flags & ~(FIF_Q_NEAREST | FIF_Q_WORLD | FIF_Q_METRICS)) return FIF_EINVAL;
     if ((flags & FIF_Q_METRICS) && !d_metrics && !d_sign && !d_status) return FIF_EINVAL;
-    if (field->storage != FIF_STORAGE_F32) return FIF_EINVAL;
     if (m == 0) return FIF_OK;
     if (reinterpret_cast<uintptr_t>(d_poses) & 3u) return FIF_EALIGN;
     fif::QueryArgs a = query_args(field, d_poses, m, flags);

@@ -27,6 +27,21 @@ struct Layout<4> {
     static constexpr int kPairBytes = 2 * kNodeBytes;   // 1728
     static constexpr int kPoseBytes = 7296;             // 57 * 128
     __device__ static constexpr int slot(int P) { return P * 1792 + (P == 0 ? 0 : P == 1 ? 16 : P == 2 ? 64 : 80); }
+    __device__ static float load(const unsigned char* p, int idx) { return reinterpret_cast<const float*>(p)[idx]; }
+};
+// bfloat16 storage: 224 elements (448 B) per node, pair 896 B; the corners of pair P start at
+// residues 16 P and 16 P + 64 modulo 128 B, so the 8 corners occupy distinct 16-B bank groups
+// and a lane's 4 consecutive 2-byte entries (at most 3 words) never collide with another corner
+template <>
+struct Layout<2> {
+    static constexpr int kStride = 224;
+    static constexpr int kNodeBytes = kStride * 2;      // 448
+    static constexpr int kPairBytes = 2 * kNodeBytes;   // 896
+    static constexpr int kPoseBytes = 4096;
+    __device__ static constexpr int slot(int P) { return P * 1024 + 16 * P; }
+    __device__ static float load(const unsigned char* p, int idx) {
+        return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(p)[idx]);
+    }
 };
 
 

@@ -294,13 +294,13 @@ __global__ void __launch_bounds__((NG + NM) * 32, 1) query_kernel(QueryArgs args
                 float vrj[10];
 #pragma unroll
                 for (int kk = 0; kk < 10; ++kk) vrj[kk] = wj * pe.vr[kk];
-                const float* C = reinterpret_cast<const float*>(G.stage[s] + corner_off) + q;
+                const unsigned char* C = G.stage[s] + corner_off;
                 float v[6];
 #pragma unroll
                 for (int ii = 0; ii < 6; ++ii) {
                     float acc = 0.f;
 #pragma unroll
-                    for (int kk = 0; kk < 10; ++kk) acc = fmaf(vrj[kk], C[kk * 21 + 4 * ii], acc);
+                    for (int kk = 0; kk < 10; ++kk) acc = fmaf(vrj[kk], L::load(C, kk * 21 + 4 * ii + q), acc);
                     v[ii] = acc;
                 }
 #pragma unroll
@@ -433,10 +433,10 @@ __global__ void __launch_bounds__((NG + NM) * 32, 1) query_kernel(QueryArgs args
 
 }  // namespace
 
-template <int NG, int NM, int NS, int NP>
+template <int kElem, int NG, int NM, int NS, int NP>
 int launch_query_cfg(const QueryArgs& a, cudaStream_t stream) {
-    auto kern = query_kernel<4, NG, NM, NS, NP>;
-    const int smem = NG * gather_smem_bytes<4, NS>();
+    auto kern = query_kernel<kElem, NG, NM, NS, NP>;
+    const int smem = NG * gather_smem_bytes<kElem, NS>();
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return FIF_ECUDA;
     int dev = 0, sms = 0;
@@ -451,7 +451,8 @@ int launch_query_cfg(const QueryArgs& a, cudaStream_t stream) {
 }
 
 int launch_query(const QueryArgs& a, cudaStream_t stream) {
-    return launch_query_cfg<kGather, kMetric, kStages, kPrefetch>(a, stream);
+    if (a.storage == FIF_STORAGE_BF16) return launch_query_cfg<2, 8, 4, 3, 4>(a, stream);
+    return launch_query_cfg<4, kGather, kMetric, kStages, kPrefetch>(a, stream);
 }
 
 }  // namespace fif

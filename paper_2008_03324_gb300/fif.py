@@ -235,6 +235,15 @@ class Field:
     def n_nodes(self):
         return self.coeffs.shape[0]
 
+    def with_params(self, params: Params) -> "Field":
+        """The same coefficient storage queried with other parameters (the stored factor does not
+        depend on the visibility coefficients, only the query does)."""
+        other = object.__new__(Field)
+        other.__dict__.update(self.__dict__)
+        other.params = params
+        other.c = field_init(self.grid, params, self.storage, self.coeffs)
+        return other
+
     def build(self, landmarks: torch.Tensor, workspace: torch.Tensor | None = None, stream=None):
         need = build_workspace_bytes(self.c, landmarks.shape[0])
         if workspace is None or workspace.numel() * workspace.element_size() < need:

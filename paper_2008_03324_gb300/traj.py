@@ -1,0 +1,46 @@
+"""Differentiable trajectory batch on the field: cubic B-spline positions with per-sample yaw,
+cameras looking horizontally, objective sum of -log det I over the samples (Sec. VII-B uses
+the information metrics of sampled poses as the perception cost of trajectory optimisation).
+
+The trajectory parameterisation (a linear B-spline map and the yaw-to-quaternion map) is the
+planner's side and runs in PyTorch; the FIM, its log-determinant and their derivatives with
+respect to the sampled positions and an so(3) perturbation of every sample come from the
+library (FifQuery -> fif_query / fif_query_backward).
+"""
+from __future__ import annotations
+
+import math
+
+import torch
+
+from . import fif
+
+# R_wc of a camera looking along +x with image y = -world z: columns (0,-1,0), (0,0,-1), (1,0,0)
+_Q0 = (0.5, -0.5, 0.5, -0.5)   # (w, x, y, z)
+
+
+def horizontal_quats(yaw: torch.Tensor) -> torch.Tensor:
+    """Unit quaternions (w, x, y, z) of cameras looking horizontally along `yaw` (rotation about
+    world z applied to the reference camera)."""
+    h = 0.5 * yaw
+    c, s = torch.cos(h), torch.sin(h)
+    w0, x0, y0, z0 = _Q0
+    # (c, 0, 0, s) (x) (w0, x0, y0, z0)
+    return torch.stack([c * w0 - s * z0, c * x0 - s * y0, c * y0 + s * x0, c * z0 + s * w0], dim=-1)
+
+
+def neg_logdet_objective(ctrl: torch.Tensor, yaw_ctrl: torch.Tensor, basis: torch.Tensor, field: fif.Field,
+                         flags: int = fif.Q_METRICS):
+    """ctrl [T, C, 3], yaw_ctrl [T, C], basis [S, C] -> (loss, phi, met, sign).
+
+    loss = sum over samples with det > 0 of -log det I (camera frame).  `phi` [T*S, 3] is the
+    zero so(3) perturbation of every sample; after loss.backward() it holds d loss / d phi."""
+    T, C, _ = ctrl.shape
+    t = torch.einsum("sc,tcd->tsd", basis, ctrl).reshape(-1, 3)
+    yaw = (yaw_ctrl @ basis.T).reshape(-1)
+    quat = horizontal_quats(yaw)
+    phi = torch.zeros(t.shape[0], 3, device=t.device, dtype=t.dtype, requires_grad=True)
+    met, sg, st = fif.FifQuery.apply(t.contiguous(), phi, quat.contiguous(), field, flags)
+    mask = (sg > 0).to(met.dtype)
+    loss = -(met[:, 1].nan_to_num() * mask).sum()
+    return loss, phi, met, sg

@@ -97,3 +97,27 @@ def metric_tolerances(I_ref, tau):
     n = fro(I_ref)
     inv = np.array([fro(np.linalg.pinv(M)) for M in I_ref])
     return math.sqrt(6) * tau * n, tau * n, 2.0 * tau * n * inv
+
+
+def round_bf16(x):
+    """Round float64/float32 values to the nearest bfloat16 (ties to even), returned as float64."""
+    f = np.ascontiguousarray(x, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1
+    u = ((u + 0x7FFF + lsb) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def local_to_world(F_local, spec):
+    """Node-local coefficients [N, 10, 6, 6] -> the paper's world frame, C^w = M_c^T C M_c (FP64)."""
+    N = F_local.shape[0]
+    idx = np.arange(N)
+    nx, ny = spec.dims[0], spec.dims[1]
+    c = np.stack([spec.origin[0] + spec.res * (idx % nx), spec.origin[1] + spec.res * ((idx // nx) % ny),
+                  spec.origin[2] + spec.res * (idx // (nx * ny))], axis=1)
+    M = np.tile(np.eye(6), (N, 1, 1))
+    S = np.zeros((N, 3, 3))
+    S[:, 0, 1], S[:, 0, 2], S[:, 1, 2] = -c[:, 2], c[:, 1], -c[:, 0]
+    S[:, 1, 0], S[:, 2, 0], S[:, 2, 1] = c[:, 2], -c[:, 1], c[:, 0]
+    M[:, :3, 3:] = -S
+    return np.einsum("nji,nkjl,nlm->nkim", M, F_local, M)

@@ -133,3 +133,33 @@ def test_query_is_deterministic(F):
     b = field.query(poses)
     for x, y in zip(a, b):
         assert torch.equal(x.nan_to_num(), y.nan_to_num())
+
+
+def test_bf16_storage_query_exact_arithmetic(F):
+    """BF16 storage: upload the oracle field rounded to bfloat16, then the GPU query must match the
+    FP64 oracle query of that same rounded field at the FP32 bound (only the storage rounds)."""
+    spec = X.ROOM["grid"]
+    F_loc = X.round_bf16(X.room_field_oracle(True))
+    field = F.Field(spec.origin, spec.res, spec.dims, F.make_params(r_max=8.0), storage=F.STORAGE_BF16)
+    buf = np.zeros((F_loc.shape[0], 224), np.float32)
+    buf[:, :210] = F_loc[:, :, X.SYM_R, X.SYM_C].reshape(-1, 210)
+    field.coeffs.copy_(torch.from_numpy(buf).to(torch.bfloat16))
+    poses = X.room_poses(1000)
+    fim, met, sg, st = run(F, field, poses)
+    Fw = X.local_to_world(F_loc, spec)
+    grid = X.oracle_grid(spec)
+    nodes, w, dw, _ = O.query_cells(grid, poses)
+    I_ref = O.query(Fw[nodes], w, poses, O.quad_coeffs(math.pi / 4, 0.5))
+    assert X.rel_fro(X.unpack21(fim), I_ref).max() <= X.TAU_F32
+
+
+def test_bf16_build_and_query_vs_fp64_oracle(F):
+    """BF16 end to end (GPU build into bfloat16 storage, GPU query) vs the FP64 oracle: <= 1e-2."""
+    sc = X.room_scene()
+    spec = X.ROOM["grid"]
+    field = F.Field(spec.origin, spec.res, spec.dims, F.make_params(r_max=8.0), storage=F.STORAGE_BF16)
+    field.build(torch.from_numpy(sc.landmarks).cuda())
+    poses = X.room_poses(1000)
+    fim, met, sg, st = run(F, field, poses)
+    I_ref, _ = oracle_query(poses)
+    assert X.rel_fro(X.unpack21(fim), I_ref).max() <= X.TAU_BF16
