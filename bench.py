@@ -224,6 +224,7 @@ def main():
                     help="build: time only the build; query: build once untimed, time only the query")
     ap.add_argument("--build-nz", type=int, default=40, help="lattice z-layers (smaller for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-large", action="store_true", help="skip the 2M-landmark building map")
     ap.add_argument("--serve-requests", type=int, default=1500)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -385,6 +386,29 @@ def main():
     out["trajopt"] = {"trajectories": 256, "samples": 128, "poses": 256 * 128, "v_alpha": 0.8,
                       "ms_forward_backward": float(np.mean(ttj)),
                       "poses_per_s": 256 * 128 / (float(np.mean(ttj)) * 1e-3)}
+
+    # ---------------- large map: 2M landmarks, 400 x 400 x 80 nodes (12.8M), r_max 12 m ----------------
+    if not args.no_large:
+        del field08
+        bscene = synth.building(seed=5, n=2_000_000)
+        bspec = synth.BUILDING_GRID
+        blm = torch.from_numpy(bscene.landmarks).to(dev)
+        large = {"landmarks": int(blm.shape[0]), "field_nodes": bspec.n_nodes, "r_max": 12.0}
+        for storage, name in ((fif.STORAGE_F32, "f32"), (fif.STORAGE_BF16, "bf16")):
+            bf = fif.Field(bspec.origin, bspec.res, bspec.dims, fif.make_params(r_max=12.0, v_alpha=0.5),
+                           storage=storage)
+            bws = torch.empty(fif.build_workspace_bytes(bf.c, blm.shape[0]), dtype=torch.uint8, device=dev)
+            tbl = time_events(lambda: fif.build(bf.c, blm, bws), 1, 0, stream)
+            ins, cnd, _ = fif.build_stats(bws, bf, blm.shape[0])
+            bposes = torch.from_numpy(synth.random_poses(77, m, bspec.lo, bspec.hi)).to(dev)
+            tql = time_events(lambda: fif.query(bf.c, bposes, fif.Q_METRICS, fim, met, sg, st), 5, 2, stream)
+            large[name] = {"build_ms": float(tbl[0]), "in_shell_pairs": ins, "build_pairs_per_s": ins / (tbl[0] * 1e-3),
+                           "field_bytes": bf.coeffs.numel() * bf.coeffs.element_size(),
+                           "queries_per_s": m / (float(np.mean(tql)) * 1e-3)}
+            del bf, bws, bposes
+            torch.cuda.empty_cache()
+        out["large"] = large
+        assert fif.device_error() == 0
 
     # ---------------- serving (rank 0) ----------------
     if rank == 0 and args.serve_requests > 0:

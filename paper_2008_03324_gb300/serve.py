@@ -5,19 +5,19 @@ loop admits a request when a slot is free and its bytes fit the in-flight memory
 packs every admitted request into the next batch (one pinned host buffer, one host-to-device
 copy, one fif_query launch, one device-to-host copy of the metrics) and keeps up to `streams`
 batches in flight on separate CUDA streams, so requests that arrive while a batch runs join
-the next one.  Completion is detected by polling CUDA events with a deadline (no blocking
+the next one.  Completion is detected by polling CUDA events against a deadline (no blocking
 waits).  Every result is independent of the batch it travelled in: the query of a pose
 depends on that pose only.
+
+The scheduler (`Scheduler`) is separate from the executor that owns the streams and buffers
+(`CudaExecutor`), so admission, batching and deadlines can be exercised without a GPU.
 """
 from __future__ import annotations
 
 import time
-from dataclasses import dataclass, field as dfield
+from dataclasses import dataclass
 
 import numpy as np
-import torch
-
-from . import fif
 
 BYTES_PER_POSE = 7 * 4 + 3 * 8 + 1 + 4   # pose in; metrics, sign, status out
 
@@ -36,34 +36,23 @@ class Result:
         return self.done - self.arrival
 
 
-@dataclass
-class _Batch:
-    stream: torch.cuda.Stream
-    event: torch.cuda.Event
-    reqs: list
-    offsets: list
-    n: int
-    launched: float
-    slot: int = 0
-
-
 class AdmissionError(RuntimeError):
     pass
 
 
-class FifServer:
-    def __init__(self, fld: fif.Field, max_batch_poses: int = 1 << 18, slots: int = 256,
-                 mem_budget_bytes: int = 64 << 20, streams: int = 2, flags: int = fif.Q_METRICS,
-                 deadline_s: float = 10.0):
+class CudaExecutor:
+    """Streams, pinned staging and device buffers for `n_streams` batches in flight."""
+
+    def __init__(self, fld, max_batch_poses: int, n_streams: int = 2, flags=None):
+        import torch
+        from . import fif
+        self.torch, self.fif = torch, fif
         self.field = fld
+        self.flags = fif.Q_METRICS if flags is None else flags
         self.max_batch = int(max_batch_poses)
-        self.slots = int(slots)
-        self.mem_budget = int(mem_budget_bytes)
-        self.flags = flags
-        self.deadline = deadline_s
         dev = fld.coeffs.device
         self.bufs = []
-        for _ in range(streams):
+        for _ in range(n_streams):
             self.bufs.append(dict(
                 stream=torch.cuda.Stream(device=dev),
                 h_pose=torch.empty(self.max_batch, 7, dtype=torch.float32, pin_memory=True),
@@ -74,16 +63,60 @@ class FifServer:
                 d_met=torch.empty(self.max_batch, 3, dtype=torch.float64, device=dev),
                 d_sg=torch.empty(self.max_batch, dtype=torch.int8, device=dev),
                 d_st=torch.empty(self.max_batch, dtype=torch.int32, device=dev),
-                busy=False,
+                event=None,
             ))
+        self.launches = 0
+
+    @property
+    def n_streams(self):
+        return len(self.bufs)
+
+    def launch(self, slot: int, batch):
+        """batch: list of [L, 7] float32 arrays packed back to back."""
+        torch, fif = self.torch, self.fif
+        b = self.bufs[slot]
+        n = 0
+        for poses in batch:
+            L = poses.shape[0]
+            b["h_pose"][n:n + L].copy_(torch.from_numpy(poses))
+            n += L
+        s = b["stream"]
+        with torch.cuda.stream(s):
+            b["d_pose"][:n].copy_(b["h_pose"][:n], non_blocking=True)
+            fif.query(self.field.c, b["d_pose"][:n], self.flags, None, b["d_met"][:n], b["d_sg"][:n],
+                      b["d_st"][:n], stream=s)
+            b["h_met"][:n].copy_(b["d_met"][:n], non_blocking=True)
+            b["h_sg"][:n].copy_(b["d_sg"][:n], non_blocking=True)
+            b["h_st"][:n].copy_(b["d_st"][:n], non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(s)
+        b["event"] = ev
+        self.launches += 1
+
+    def done(self, slot: int) -> bool:
+        return self.bufs[slot]["event"].query()
+
+    def results(self, slot: int, off: int, L: int):
+        b = self.bufs[slot]
+        return (b["h_met"][off:off + L].numpy().copy(), b["h_sg"][off:off + L].numpy().copy(),
+                b["h_st"][off:off + L].numpy().copy())
+
+
+class Scheduler:
+    """Admission by slots and an in-flight memory budget; continuous batching over the
+    executor's streams; completion polling with a per-batch deadline."""
+
+    def __init__(self, executor, slots: int = 256, mem_budget_bytes: int = 64 << 20, deadline_s: float = 10.0):
+        self.ex = executor
+        self.slots = int(slots)
+        self.mem_budget = int(mem_budget_bytes)
+        self.deadline = float(deadline_s)
         self.in_use_slots = 0
         self.in_use_bytes = 0
         self.peak_bytes = 0
         self.peak_slots = 0
         self.batches_launched = 0
-        self.kernel_launches = 0
 
-    # ---- admission ----------------------------------------------------------------
     def _fits(self, n):
         return self.in_use_slots < self.slots and self.in_use_bytes + n * BYTES_PER_POSE <= self.mem_budget
 
@@ -97,59 +130,21 @@ class FifServer:
         self.in_use_slots -= 1
         self.in_use_bytes -= n * BYTES_PER_POSE
 
-    # ---- batches --------------------------------------------------------------------
-    def _launch(self, bi, reqs, now):
-        b = self.bufs[bi]
-        offs, n = [], 0
-        for (_, poses) in reqs:
-            L = poses.shape[0]
-            b["h_pose"][n:n + L].copy_(torch.from_numpy(poses))
-            offs.append(n)
-            n += L
-        s = b["stream"]
-        with torch.cuda.stream(s):
-            b["d_pose"][:n].copy_(b["h_pose"][:n], non_blocking=True)
-            fif.query(self.field.c, b["d_pose"][:n], self.flags, None, b["d_met"][:n], b["d_sg"][:n],
-                      b["d_st"][:n], stream=s)
-            b["h_met"][:n].copy_(b["d_met"][:n], non_blocking=True)
-            b["h_sg"][:n].copy_(b["d_sg"][:n], non_blocking=True)
-            b["h_st"][:n].copy_(b["d_st"][:n], non_blocking=True)
-            ev = torch.cuda.Event()
-            ev.record(s)
-        b["busy"] = True
-        self.batches_launched += 1
-        self.kernel_launches += 1
-        return _Batch(stream=s, event=ev, reqs=reqs, offsets=offs, n=n, launched=now, slot=bi)
-
-    def _complete(self, batch, results, now):
-        b = self.bufs[batch.slot]
-        for (rid, poses), off in zip(batch.reqs, batch.offsets):
-            L = poses.shape[0]
-            r = results[rid]
-            r.metrics = b["h_met"][off:off + L].numpy().copy()
-            r.sign = b["h_sg"][off:off + L].numpy().copy()
-            r.status = b["h_st"][off:off + L].numpy().copy()
-            r.done = now
-            self._release(L)
-        b["busy"] = False
-
-    def run(self, requests, arrivals=None, clock=time.perf_counter):
-        """Serve `requests` (list of [L, 7] float32 arrays) arriving at `arrivals` seconds
-        (open loop; None = all at t=0).  Returns the list of Result in request order."""
+    def run(self, requests, arrivals=None, clock=time.perf_counter, sleep=time.sleep):
+        """Serve `requests` (list of [L, 7] float32 arrays) arriving at `arrivals` seconds (open
+        loop; None = all at t = 0).  Returns the list of Result in request order."""
         n_req = len(requests)
         if arrivals is None:
             arrivals = np.zeros(n_req)
         order = np.argsort(arrivals, kind="stable")
         for r in requests:
-            if r.shape[0] > self.max_batch or r.shape[0] * BYTES_PER_POSE > self.mem_budget:
+            if r.shape[0] > self.ex.max_batch or r.shape[0] * BYTES_PER_POSE > self.mem_budget:
                 raise AdmissionError(f"request of {r.shape[0]} poses exceeds the batch or memory limit")
         results = [Result(np.zeros((0, 3)), np.zeros(0, np.int8), np.zeros(0, np.int32)) for _ in range(n_req)]
         t0 = clock()
-        nxt = 0                  # next request (in arrival order) not yet arrived
-        waiting = []             # arrived, not admitted
-        ready = []               # admitted, not launched
-        inflight = []
-        done = 0
+        nxt, done = 0, 0
+        waiting, ready = [], []
+        inflight = {}            # stream slot -> (request ids, offsets, launch time)
         while done < n_req:
             now = clock() - t0
             while nxt < n_req and arrivals[order[nxt]] <= now:
@@ -162,32 +157,48 @@ class FifServer:
                 self._admit(requests[rid].shape[0])
                 results[rid].admitted = now
                 ready.append(rid)
-            # complete finished batches
-            still = []
-            for b in inflight:
-                if b.event.query():
-                    self._complete(b, results, clock() - t0)
-                    done += len(b.reqs)
-                elif now - b.launched > self.deadline:
-                    raise TimeoutError(f"batch of {b.n} poses exceeded {self.deadline} s ({fif.status_str(fif.ETIMEOUT)})")
-                else:
-                    still.append(b)
-            inflight = still
-            # launch on a free stream
-            free = [i for i, b in enumerate(self.bufs) if not b["busy"]]
+            for slot in list(inflight):
+                rids, offs, launched = inflight[slot]
+                if self.ex.done(slot):
+                    tdone = clock() - t0
+                    for rid, off in zip(rids, offs):
+                        L = requests[rid].shape[0]
+                        r = results[rid]
+                        r.metrics, r.sign, r.status = self.ex.results(slot, off, L)
+                        r.done = tdone
+                        self._release(L)
+                    done += len(rids)
+                    del inflight[slot]
+                elif now - launched > self.deadline:
+                    raise TimeoutError(f"batch on stream {slot} exceeded the {self.deadline} s deadline")
+            free = [s for s in range(self.ex.n_streams) if s not in inflight]
             if ready and free:
-                take, n = [], 0
-                while ready and n + requests[ready[0]].shape[0] <= self.max_batch:
+                rids, offs, n = [], [], 0
+                while ready and n + requests[ready[0]].shape[0] <= self.ex.max_batch:
                     rid = ready.pop(0)
-                    take.append((rid, requests[rid]))
+                    rids.append(rid)
+                    offs.append(n)
                     n += requests[rid].shape[0]
-                inflight.append(self._launch(free[0], take, clock() - t0))
-            elif not inflight and not ready and nxt < n_req and not waiting:
-                # idle until the next arrival
+                self.ex.launch(free[0], [requests[r] for r in rids])
+                self.batches_launched += 1
+                inflight[free[0]] = (rids, offs, clock() - t0)
+            elif not inflight and not ready and not waiting and nxt < n_req:
                 dt = arrivals[order[nxt]] - (clock() - t0)
                 if dt > 2e-4:
-                    time.sleep(dt - 1e-4)
+                    sleep(dt - 1e-4)
         return results
+
+
+class FifServer(Scheduler):
+    """Scheduler + CUDA executor over a device-resident field."""
+
+    def __init__(self, fld, max_batch_poses: int = 1 << 18, slots: int = 256, mem_budget_bytes: int = 64 << 20,
+                 streams: int = 2, flags=None, deadline_s: float = 10.0):
+        super().__init__(CudaExecutor(fld, max_batch_poses, streams, flags), slots, mem_budget_bytes, deadline_s)
+
+    @property
+    def kernel_launches(self):
+        return self.ex.launches
 
 
 def latency_stats(results):

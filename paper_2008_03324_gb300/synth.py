@@ -79,15 +79,38 @@ def _area(r):
     return float(np.linalg.norm(r[1]) * np.linalg.norm(r[2]))
 
 
-def _inside_any(points, boxes, margin=1e-6):
-    if len(boxes) == 0:
-        return np.zeros(len(points), bool)
-    inside = np.zeros(len(points), bool)
-    for lo, hi in boxes:
-        lo = np.asarray(lo) + margin
-        hi = np.asarray(hi) - margin
-        inside |= np.all((points > lo) & (points < hi), axis=1)
-    return inside
+def _inside_any(points, boxes, margin=1e-6, cell=4.0):
+    """True for points strictly inside any of the boxes (boxes bucketed on a 2-D grid of
+    `cell`-metre squares so each point is tested against the few boxes near it)."""
+    points = np.asarray(points)
+    out = np.zeros(len(points), bool)
+    if len(boxes) == 0 or len(points) == 0:
+        return out
+    lo = np.array([b[0] for b in boxes], dtype=np.float64) + margin   # [B, 3]
+    hi = np.array([b[1] for b in boxes], dtype=np.float64) - margin
+    x0, y0 = lo[:, 0].min(), lo[:, 1].min()
+    nx = int(np.ceil((hi[:, 0].max() - x0) / cell)) + 1
+    ny = int(np.ceil((hi[:, 1].max() - y0) / cell)) + 1
+    buckets = {}
+    for b in range(len(boxes)):
+        for i in range(int((lo[b, 0] - x0) // cell), int((hi[b, 0] - x0) // cell) + 1):
+            for j in range(int((lo[b, 1] - y0) // cell), int((hi[b, 1] - y0) // cell) + 1):
+                buckets.setdefault(i + nx * j, []).append(b)
+    ix = np.floor((points[:, 0] - x0) / cell).astype(np.int64)
+    iy = np.floor((points[:, 1] - y0) / cell).astype(np.int64)
+    valid = (ix >= 0) & (ix < nx) & (iy >= 0) & (iy < ny)
+    cid = np.where(valid, ix + nx * iy, -1)
+    order = np.argsort(cid, kind="stable")
+    cs = cid[order]
+    starts = np.searchsorted(cs, list(buckets.keys()), side="left")
+    stops = np.searchsorted(cs, list(buckets.keys()), side="right")
+    for (key, bl), a, z in zip(buckets.items(), starts, stops):
+        if z <= a:
+            continue
+        idx = order[a:z]
+        p = points[idx][:, None, :]
+        out[idx] = np.any(np.all((p > lo[bl]) & (p < hi[bl]), axis=2), axis=1)
+    return out
 
 
 def _sample_surfaces(rng, rects, weights, n, boxes, jitter):

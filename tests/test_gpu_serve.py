@@ -1,0 +1,29 @@
+"""The serving loop on the GPU: each request's metrics are bitwise identical alone and inside a
+mixed stream of requests (the query of a pose depends on that pose only)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2008_03324_gb300 import synth
+from tests import _fixtures as X
+
+pytestmark = pytest.mark.gpu
+
+
+def test_alone_equals_mixed_on_gpu():
+    from paper_2008_03324_gb300 import build as B
+    B.build()
+    from paper_2008_03324_gb300 import fif, serve
+    spec = X.ROOM["grid"]
+    field = fif.Field(spec.origin, spec.res, spec.dims, fif.make_params(r_max=8.0))
+    field.coeffs.copy_(torch.from_numpy(X.pack_field(X.room_field_oracle(True))))
+    room = synth.Scene("room", X.room_scene().landmarks, np.zeros(3), np.array([10.0, 10.0, 3.0]), [])
+    reqs = synth.request_stream(8, 120, room, zr=(0.5, 2.5), max_len=512)
+    srv = serve.FifServer(field, max_batch_poses=1 << 14, slots=32, mem_budget_bytes=1 << 20)
+    mixed = srv.run(reqs, synth.poisson_arrivals(9, len(reqs), 5000.0))
+    assert srv.peak_bytes <= 1 << 20 and srv.batches_launched < len(reqs)
+    for i in (0, 17, 63, 119):
+        alone = serve.FifServer(field, max_batch_poses=1 << 14).run([reqs[i]])[0]
+        np.testing.assert_array_equal(np.nan_to_num(alone.metrics), np.nan_to_num(mixed[i].metrics))
+        np.testing.assert_array_equal(alone.sign, mixed[i].sign)
+        np.testing.assert_array_equal(alone.status, mixed[i].status)

@@ -1,0 +1,115 @@
+"""Host-side logic of the continuous-batching loop (no GPU): admission by slots and memory,
+batching of requests that arrive while others run, result routing, and the deadline path."""
+import numpy as np
+import pytest
+
+from paper_2008_03324_gb300 import serve
+
+
+class FakeExecutor:
+    """Completes a batch after `latency` polls; the 'metric' of a pose is a function of that
+    pose only, so a request's result must not depend on its batch."""
+
+    def __init__(self, max_batch=1000, n_streams=2, latency=3, never=False):
+        self.max_batch, self.n_streams, self.latency, self.never = max_batch, n_streams, latency, never
+        self.polls = {}
+        self.data = {}
+        self.batches = []
+
+    def launch(self, slot, batch):
+        poses = np.concatenate(batch, axis=0)
+        self.batches.append([b.shape[0] for b in batch])
+        self.data[slot] = poses
+        self.polls[slot] = 0
+
+    def done(self, slot):
+        self.polls[slot] += 1
+        return (not self.never) and self.polls[slot] >= self.latency
+
+    def results(self, slot, off, L):
+        p = self.data[slot][off:off + L].astype(np.float64)
+        met = np.stack([p.sum(1), p[:, 0] * 2, p[:, 1] - p[:, 2]], axis=1)
+        return met, np.sign(p[:, 3]).astype(np.int8), np.arange(off, off + L, dtype=np.int32) * 0
+
+
+class FakeClock:
+    def __init__(self, step=1e-4):
+        self.t, self.step = 0.0, step
+
+    def __call__(self):
+        self.t += self.step
+        return self.t
+
+    def sleep(self, dt):
+        self.t += dt
+
+
+def make_requests(seed, n, lo=8, hi=200):
+    rng = np.random.default_rng(seed)
+    return [rng.standard_normal((int(rng.integers(lo, hi)), 7)).astype(np.float32) for _ in range(n)]
+
+
+def expected(r):
+    p = r.astype(np.float64)
+    return np.stack([p.sum(1), p[:, 0] * 2, p[:, 1] - p[:, 2]], axis=1)
+
+
+def test_results_are_routed_to_their_requests():
+    reqs = make_requests(1, 60)
+    ex = FakeExecutor()
+    sch = serve.Scheduler(ex, slots=16, mem_budget_bytes=1 << 20)
+    clk = FakeClock()
+    arr = np.cumsum(np.full(60, 2e-4))
+    res = sch.run(reqs, arr, clock=clk, sleep=clk.sleep)
+    for r, q in zip(res, reqs):
+        np.testing.assert_array_equal(r.metrics, expected(q))
+        assert r.done >= r.arrival and r.latency >= 0
+    assert sum(len(b) for b in ex.batches) == 60
+
+
+def test_same_result_alone_and_in_a_mix():
+    reqs = make_requests(2, 40)
+    alone = serve.Scheduler(FakeExecutor(), slots=64).run([reqs[7]])[0]
+    mixed = serve.Scheduler(FakeExecutor(), slots=64).run(reqs)[7]
+    np.testing.assert_array_equal(alone.metrics, mixed.metrics)
+    np.testing.assert_array_equal(alone.sign, mixed.sign)
+
+
+def test_admission_never_exceeds_slots_or_memory():
+    reqs = make_requests(3, 200, 50, 400)
+    budget = 30_000
+    ex = FakeExecutor(max_batch=500, latency=5)
+    sch = serve.Scheduler(ex, slots=4, mem_budget_bytes=budget)
+    clk = FakeClock()
+    res = sch.run(reqs, None, clock=clk, sleep=clk.sleep)
+    assert sch.peak_bytes <= budget and sch.peak_slots <= 4
+    assert sch.in_use_bytes == 0 and sch.in_use_slots == 0
+    for r, q in zip(res, reqs):
+        np.testing.assert_array_equal(r.metrics, expected(q))
+
+
+def test_requests_arriving_during_a_batch_join_the_next():
+    """Continuous batching: with one stream busy, everything that arrives meanwhile goes out
+    together in the next batch instead of one launch per request."""
+    reqs = make_requests(4, 30, 10, 20)
+    ex = FakeExecutor(max_batch=10_000, n_streams=1, latency=50)
+    clk = FakeClock(step=1e-4)
+    arr = np.linspace(0.0, 0.004, 30)
+    serve.Scheduler(ex, slots=64).run(reqs, arr, clock=clk, sleep=clk.sleep)
+    assert len(ex.batches) < 30
+    assert max(len(b) for b in ex.batches) > 1
+
+
+def test_oversized_request_is_refused():
+    ex = FakeExecutor(max_batch=100)
+    with pytest.raises(serve.AdmissionError):
+        serve.Scheduler(ex).run([np.zeros((101, 7), np.float32)])
+    with pytest.raises(serve.AdmissionError):
+        serve.Scheduler(FakeExecutor(max_batch=10_000), mem_budget_bytes=1000).run([np.zeros((100, 7), np.float32)])
+
+
+def test_deadline_raises_instead_of_hanging():
+    ex = FakeExecutor(never=True)
+    clk = FakeClock(step=0.01)
+    with pytest.raises(TimeoutError):
+        serve.Scheduler(ex, deadline_s=0.5).run(make_requests(5, 3), None, clock=clk, sleep=clk.sleep)
