@@ -369,6 +369,18 @@ def main():
     del field16
     torch.cuda.empty_cache()
 
+    # ---------------- positional trace factor (10 floats per node, world-frame trace) ----------------
+    ftr = fif.Field(spec.origin, spec.res, spec.dims, params, storage=fif.STORAGE_TRACE)
+    ttb = time_events(lambda: fif.build(ftr.c, lm, wsb), 2, 1, stream)
+    ttq = time_events(lambda: fif.query(ftr.c, poses, fif.Q_TRACE | fif.Q_WORLD, None, met, None, st), 10, 3,
+                      stream)
+    btr = 8 * 10 * 4 + 7 * 4 + 8 + 4
+    out["trace_field"] = {"field_bytes": ftr.coeffs.numel() * 4, "build_ms": float(np.mean(ttb)),
+                          "queries_per_s": m / (float(np.mean(ttq)) * 1e-3), "bytes_per_pose": btr,
+                          "roofline": {"bound": "hbm", "achieved": m * btr / (float(np.mean(ttq)) * 1e-3) / 1e9,
+                                       "peak": hbm_peak, "unit": "GB/s"}}
+    del ftr
+
     # ---------------- differentiable trajectory batch (256 x 128 samples) ----------------
     from paper_2008_03324_gb300 import traj
     ctrl_np, yaw_np, basis_np = synth.bspline_batch(6, scene, 256, 32, 128)

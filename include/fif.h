@@ -70,6 +70,10 @@ typedef struct CUstream_st* fif_stream_t;
 /* ---- storage of the field ------------------------------------------------------------ */
 #define FIF_STORAGE_F32 0    /* float32, 216 elements (864 B) per node                  */
 #define FIF_STORAGE_BF16 1   /* bfloat16 (round to nearest even), 224 elements (448 B)    */
+#define FIF_STORAGE_TRACE 2  /* the positional trace factor of Sec. VI-A-2 (Eq.             */
+                             /* general_trace_pif): float32 tr(C_k^world), k = 0..9, plus 2 */
+                             /* zero pads = 12 elements (48 B) per node; fif_query then      */
+                             /* returns only the world-frame trace (FIF_Q_TRACE | FIF_Q_WORLD)*/
 
 /* ---- query flags ---------------------------------------------------------------------- */
 #define FIF_Q_TRILINEAR 0x0  /* interpolate over the 8 surrounding nodes (default)        */
@@ -127,7 +131,9 @@ typedef struct fif_pinhole {
  * from the node to landmark i, I_i its information (Eq. global_fim_eq) with the
  * rotational part of the perturbation taken about the node itself (the paper's world
  * frame moved to the node: C^world = M_c^T C M_c, M_c = [[I, -[c]x], [0, I]]).
- * Elements 210 .. stride-1 are zero.  k[] = (k0, k1, k2) is filled by fif_field_init. */
+ * Elements 210 .. stride-1 are zero.  With FIF_STORAGE_TRACE, node n holds instead the 10 traces
+ * tr(C_k^world) (world frame: rotation about the origin) at n*12 + k, then two zeros.
+ * k[] = (k0, k1, k2) is filled by fif_field_init. */
 typedef struct fif_field {
     fif_grid grid;
     fif_params params;
@@ -165,6 +171,16 @@ FIF_API size_t fif_build_workspace_bytes(const fif_field* field, int64_t n_landm
  * fields.  Overwrites the whole storage.  n may be 0 (the field becomes zero). */
 FIF_API int32_t fif_build(fif_field* field, const float* d_landmarks, int64_t n, void* d_workspace,
                   size_t workspace_bytes, fif_stream_t stream);
+
+/* Online update of a built field (Sec. VI-A-1: the positional factor is a sum of one term per
+ * landmark, so adding or deleting a landmark adds or subtracts its term).  sign = +1 adds the
+ * n landmarks' contributions to every node they reach, sign = -1 removes them; nodes farther than
+ * r_max from all of them are not touched.  The same arithmetic as fif_build (the delta of the n
+ * landmarks is summed with compensation, then added to each stored coefficient in single
+ * precision, or rounded back to bfloat16 for that storage); moving a landmark is a removal
+ * followed by an addition.  Workspace as for fif_build with n landmarks. */
+FIF_API int32_t fif_build_update(fif_field* field, const float* d_landmarks, int64_t n, int32_t sign,
+                                 void* d_workspace, size_t workspace_bytes, fif_stream_t stream);
 
 /* Size of the fixed device scratch array that fif_build_static uses (16 MiB). */
 #define FIF_BUILD_STATIC_SCRATCH_BYTES (16u << 20)

@@ -224,6 +224,30 @@ __device__ float moment(const float* hs, const float* ls, int tid, int p, int ex
     return s;
 }
 
+// entry e (upper-triangular 6x6) of the node-local C_k, from the moments (before 1/sigma^2):
+//   TT: (delta_rc - u_r u_c)/n^2,  TR: (-[u]x)_{r b}/n = eps_{r b l} u_l / n,  RR: delta_ab - u_a u_b,
+// each times the monomial v_p[k](u)
+__device__ float coef_local(const float* hs, const float* ls, int tid, int k, int e) {
+    const int r = sym_row(e), c = sym_col(e);
+    const int mx = kVp[k][0], my = kVp[k][1], mz = kVp[k][2];
+    if (r < 3 && c < 3) {
+        float v = -moment(hs, ls, tid, 2, mx + (r == 0) + (c == 0), my + (r == 1) + (c == 1), mz + (r == 2) + (c == 2));
+        if (r == c) v += moment(hs, ls, tid, 2, mx, my, mz);
+        return v;
+    }
+    if (r < 3) {
+        const int b = c - 3;
+        if (r == b) return 0.f;
+        const int l = 3 - r - b;
+        const float sgn = ((r + 1) % 3 == b) ? 1.f : -1.f;  // eps_{r b l}
+        return sgn * moment(hs, ls, tid, 1, mx + (l == 0), my + (l == 1), mz + (l == 2));
+    }
+    const int ra = r - 3, cb = c - 3;
+    float v = -moment(hs, ls, tid, 0, mx + (ra == 0) + (cb == 0), my + (ra == 1) + (cb == 1), mz + (ra == 2) + (cb == 2));
+    if (ra == cb) v += moment(hs, ls, tid, 0, mx, my, mz);
+    return v;
+}
+
 __device__ __forceinline__ void kahan_merge(float* hs, float* ls, int idx, float x) {
     const float s = hs[idx], c = ls[idx];
     const float y = x - c;
@@ -479,48 +503,66 @@ __global__ void __launch_bounds__(kThreads, 2) build_kernel(BuildArgs a) {
         if (lane == 0) atomicAdd(&stats[1], cand * nv);
     }
     if (!valid) return;
+    // an update leaves nodes that no landmark of the delta reaches untouched
+    if (a.accumulate != 0 && cand == 0) return;
     // ---- epilogue: 66 moments -> 210 coefficients (times 1/sigma^2) ----
     const int64_t node = ni + (int64_t)a.nx * (nj + (int64_t)a.ny * nk);
+    if (a.storage == FIF_STORAGE_TRACE) {
+        // the paper's positional trace factor (Sec. VI-A-2): tr of the world-frame C_k,
+        //   tr(M_c^T C M_c) = tr(A) + tr(D) + |c|^2 tr(A) - c^T A c + 2 tr([c]x B)
+        float* dst = reinterpret_cast<float*>(a.out) + node * a.stride;
+        const float c3[3] = {cx, cy, cz};
+        const float cc = cx * cx + cy * cy + cz * cz;
+        for (int k = 0; k < 10; ++k) {
+            float val = 0.f;
+            if (ok) {
+                float A[3][3], Bm[3][3], trD = 0.f;
+                for (int e = 0; e < 21; ++e) {
+                    const float v = coef_local(hs, ls, tid, k, e) * a.inv_sigma2;
+                    const int r = sym_row(e), c = sym_col(e);
+                    if (r < 3 && c < 3) { A[r][c] = v; A[c][r] = v; }
+                    else if (r < 3) Bm[r][c - 3] = v;
+                    else if (r == c) trD += v;
+                }
+                const float trA = A[0][0] + A[1][1] + A[2][2];
+                float cAc = 0.f, cxB = 0.f;
+                for (int r = 0; r < 3; ++r)
+                    for (int c = 0; c < 3; ++c) cAc += c3[r] * A[r][c] * c3[c];
+                // [c]x = [[0, -cz, cy], [cz, 0, -cx], [-cy, cx, 0]];  tr([c]x B) = sum_ij [c]x_ij B_ji
+                const float S[3][3] = {{0.f, -cz, cy}, {cz, 0.f, -cx}, {-cy, cx, 0.f}};
+                for (int r = 0; r < 3; ++r)
+                    for (int c = 0; c < 3; ++c) cxB += S[r][c] * Bm[c][r];
+                val = trA + trD + cc * trA - cAc + 2.f * cxB;
+            }
+            if (a.accumulate != 0) val = fmaf((float)a.accumulate, val, dst[k]);
+            dst[k] = val;
+        }
+        for (int k = 10; k < a.stride; ++k) dst[k] = 0.f;
+        return;
+    }
     float outv[4];
     int filled = 0;
     for (int o = 0; o < a.stride; ++o) {
         float val = 0.f;
-        if (o < 210 && ok) {
-            const int k = o / 21, e = o % 21;
-            const int r = sym_row(e), c = sym_col(e);
-            const int mx = kVp[k][0], my = kVp[k][1], mz = kVp[k][2];
-            if (r < 3 && c < 3) {
-                // (delta_rc - u_r u_c) / n^2
-                float v = -moment(hs, ls, tid, 2, mx + (r == 0) + (c == 0), my + (r == 1) + (c == 1),
-                                  mz + (r == 2) + (c == 2));
-                if (r == c) v += moment(hs, ls, tid, 2, mx, my, mz);
-                val = v;
-            } else if (r < 3) {
-                // (-[u]x)_{r b} / n = eps_{r b l} u_l / n
-                const int b = c - 3;
-                if (r != b) {
-                    const int l = 3 - r - b;
-                    const float sgn = ((r + 1) % 3 == b) ? 1.f : -1.f;  // eps_{r b l}
-                    val = sgn * moment(hs, ls, tid, 1, mx + (l == 0), my + (l == 1), mz + (l == 2));
-                }
-            } else {
-                const int ra = r - 3, cb = c - 3;
-                float v = -moment(hs, ls, tid, 0, mx + (ra == 0) + (cb == 0), my + (ra == 1) + (cb == 1),
-                                  mz + (ra == 2) + (cb == 2));
-                if (ra == cb) v += moment(hs, ls, tid, 0, mx, my, mz);
-                val = v;
-            }
-            val *= a.inv_sigma2;
-        }
+        if (o < 210 && ok) val = coef_local(hs, ls, tid, o / 21, o % 21) * a.inv_sigma2;
         if (a.storage == FIF_STORAGE_F32) {
             outv[filled++] = val;
             if (filled == 4) {
                 float4* dst = reinterpret_cast<float4*>(reinterpret_cast<float*>(a.out) + node * a.stride + (o - 3));
-                *dst = make_float4(outv[0], outv[1], outv[2], outv[3]);
+                float4 v4 = make_float4(outv[0], outv[1], outv[2], outv[3]);
+                if (a.accumulate != 0) {
+                    const float sgn = (float)a.accumulate;
+                    const float4 old = *dst;
+                    v4 = make_float4(fmaf(sgn, v4.x, old.x), fmaf(sgn, v4.y, old.y), fmaf(sgn, v4.z, old.z),
+                                     fmaf(sgn, v4.w, old.w));
+                }
+                *dst = v4;
                 filled = 0;
             }
         } else {
-            reinterpret_cast<__nv_bfloat16*>(a.out)[node * a.stride + o] = __float2bfloat16_rn(val);
+            __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(a.out) + node * a.stride + o;
+            if (a.accumulate != 0) val = fmaf((float)a.accumulate, val, __bfloat162float(*dst));
+            *dst = __float2bfloat16_rn(val);
         }
     }
 }

@@ -32,9 +32,9 @@ int* device_error_ptr() {
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 int stride_of(int32_t storage) {
-    return storage == FIF_STORAGE_F32 ? 216 : storage == FIF_STORAGE_BF16 ? 224 : 0;
+    return storage == FIF_STORAGE_F32 ? 216 : storage == FIF_STORAGE_BF16 ? 224 : storage == FIF_STORAGE_TRACE ? 12 : 0;
 }
-size_t elem_of(int32_t storage) { return storage == FIF_STORAGE_F32 ? 4 : 2; }
+size_t elem_of(int32_t storage) { return storage == FIF_STORAGE_BF16 ? 2 : 4; }
 
 int check_grid(const fif_grid* g) {
     if (!g) return FIF_EINVAL;
@@ -167,8 +167,22 @@ size_t fif_build_workspace_bytes(const fif_field* field, int64_t n) {
     return fif::build_layout(bg, n).total;
 }
 
+static int32_t build_impl(fif_field* field, const float* d_landmarks, int64_t n, void* d_ws, size_t ws_bytes,
+                          int accumulate, fif_stream_t stream);
+
 int32_t fif_build(fif_field* field, const float* d_landmarks, int64_t n, void* d_ws, size_t ws_bytes,
                   fif_stream_t stream) {
+    return build_impl(field, d_landmarks, n, d_ws, ws_bytes, 0, stream);
+}
+
+int32_t fif_build_update(fif_field* field, const float* d_landmarks, int64_t n, int32_t sign, void* d_ws,
+                         size_t ws_bytes, fif_stream_t stream) {
+    if (sign != 1 && sign != -1) return FIF_EINVAL;
+    return build_impl(field, d_landmarks, n, d_ws, ws_bytes, sign, stream);
+}
+
+static int32_t build_impl(fif_field* field, const float* d_landmarks, int64_t n, void* d_ws, size_t ws_bytes,
+                          int accumulate, fif_stream_t stream) {
     int rc = check_field(field);
     if (rc) return rc;
     if (n < 0 || (n > 0 && !d_landmarks) || !d_ws) return FIF_EINVAL;
@@ -193,6 +207,7 @@ int32_t fif_build(fif_field* field, const float* d_landmarks, int64_t n, void* d
     a.stride = field->stride;
     a.out = field->coeffs;
     a.err = device_error_ptr();
+    a.accumulate = accumulate;
     return fif::launch_build(a, stream);
 }
 
@@ -210,6 +225,11 @@ int32_t fif_query(const fif_field* field, const float* d_poses, int64_t m, int32
     a.metrics = d_metrics;
     a.sign = d_sign;
     a.status = d_status;
+    if (field->storage == FIF_STORAGE_TRACE) {
+        // the trace factor answers only the world-frame trace (Eq. general_trace_query)
+        if ((flags & FIF_Q_METRICS) != FIF_Q_TRACE || !(flags & FIF_Q_WORLD) || d_fim || d_sign) return FIF_EINVAL;
+        return fif::launch_trace_query(a, stream);
+    }
     return fif::launch_query(a, stream);
 }
 
@@ -220,7 +240,7 @@ int32_t fif_query_backward(const fif_field* field, const float* d_poses, int64_t
     if (rc) return rc;
     if (m < 0 || (m > 0 && (!d_poses || !d_fim || !d_grad_metrics || !d_grad_pose))) return FIF_EINVAL;
     if (flags & ~(FIF_Q_WORLD | FIF_Q_METRICS)) return FIF_EINVAL;  // trilinear only
-    if (field->storage != FIF_STORAGE_F32) return FIF_EINVAL;
+    if (field->storage != FIF_STORAGE_F32) return FIF_EINVAL;  // the adjoint reads float32 coefficients
     if (m == 0) return FIF_OK;
     fif::QueryArgs q = query_args(field, d_poses, m, flags);
     fif::AdjointArgs a{};

@@ -28,6 +28,7 @@ struct QueryArgs {
     int* err;
 };
 int launch_query(const QueryArgs& a, cudaStream_t stream);
+int launch_trace_query(const QueryArgs& a, cudaStream_t stream);
 
 // ---- query adjoint -------------------------------------------------------------------
 struct AdjointArgs {
@@ -81,6 +82,7 @@ struct BuildArgs {
     int stride;
     void* out;
     int* err;
+    int accumulate;   // 0: overwrite the field; +1 / -1: add / subtract these landmarks' share
 };
 int launch_build(const BuildArgs& a, cudaStream_t stream);
 

@@ -25,10 +25,10 @@ LIB_PATH = os.path.join(_HERE, "libfif.so")
 # ---- constants (mirror include/fif.h) -------------------------------------------------
 OK, EINVAL, ESIZE, EALIGN, ECUDA, ETIMEOUT, EIO, EFORMAT, ERANGE = 0, -1, -2, -3, -4, -5, -6, -7, -8
 POSE_OUTSIDE, POSE_QUAT, POSE_NOT_PD, POSE_NAN = 1, 2, 4, 8
-STORAGE_F32, STORAGE_BF16 = 0, 1
+STORAGE_F32, STORAGE_BF16, STORAGE_TRACE = 0, 1, 2
 Q_TRILINEAR, Q_NEAREST, Q_CAMERA, Q_WORLD = 0x0, 0x1, 0x0, 0x2
 Q_TRACE, Q_LOGDET, Q_LMIN, Q_METRICS = 0x10, 0x20, 0x40, 0x70
-STRIDE = {STORAGE_F32: 216, STORAGE_BF16: 224}
+STRIDE = {STORAGE_F32: 216, STORAGE_BF16: 224, STORAGE_TRACE: 12}
 
 
 class FifError(RuntimeError):
@@ -73,6 +73,7 @@ _SIGS = {
     "fif_build_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(FieldC), _I64]),
     "fif_build": (_I32, [ctypes.POINTER(FieldC), _VP, _I64, _VP, ctypes.c_size_t, _VP]),
     "fif_build_static": (_I32, [ctypes.POINTER(FieldC), _VP, _I64, _VP]),
+    "fif_build_update": (_I32, [ctypes.POINTER(FieldC), _VP, _I64, _I32, _VP, ctypes.c_size_t, _VP]),
     "fif_query": (_I32, [ctypes.POINTER(FieldC), _VP, _I64, _I32, _VP, _VP, _VP, _VP, _VP]),
     "fif_query_backward": (_I32, [ctypes.POINTER(FieldC), _VP, _I64, _I32, _VP, _VP, _VP, _VP]),
     "fif_pointcloud_fim": (_I32, [_VP, _I64, ctypes.POINTER(Params), ctypes.POINTER(Pinhole), _VP, _I64, _I32,
@@ -164,6 +165,14 @@ def build(field: FieldC, landmarks: torch.Tensor, workspace: torch.Tensor, strea
                            workspace.numel() * workspace.element_size(), _stream(stream)), "fif_build")
 
 
+def build_update(field: FieldC, landmarks: torch.Tensor, sign: int, workspace: torch.Tensor, stream=None):
+    """Add (sign=+1) or remove (sign=-1) landmarks' contributions to a built field."""
+    assert landmarks.is_cuda and landmarks.dtype == torch.float32 and landmarks.is_contiguous()
+    _check(lib().fif_build_update(ctypes.byref(field), _ptr(landmarks), landmarks.shape[0], int(sign),
+                                  _ptr(workspace), workspace.numel() * workspace.element_size(), _stream(stream)),
+           "fif_build_update")
+
+
 BUILD_STATIC_SCRATCH_BYTES = 16 << 20
 
 
@@ -224,7 +233,7 @@ class Field:
         nbytes = field_bytes(self.grid, storage)
         if nbytes == 0:
             raise FifError(EINVAL, "fif_field_bytes")
-        dt = torch.float32 if storage == STORAGE_F32 else torch.bfloat16
+        dt = torch.bfloat16 if storage == STORAGE_BF16 else torch.float32
         n_nodes = int(dims[0]) * int(dims[1]) * int(dims[2])
         self.storage = storage
         self.coeffs = torch.zeros(n_nodes, STRIDE[storage], dtype=dt, device=device)
@@ -254,10 +263,13 @@ class Field:
     def query(self, poses, flags=Q_METRICS, want_fim=True, stream=None):
         m = poses.shape[0]
         dev = poses.device
-        fim = torch.empty(m, 21, dtype=torch.float32, device=dev) if want_fim else None
+        trace = self.storage == STORAGE_TRACE
+        fim = torch.empty(m, 21, dtype=torch.float32, device=dev) if (want_fim and not trace) else None
         met = torch.empty(m, 3, dtype=torch.float64, device=dev)
-        sg = torch.empty(m, dtype=torch.int8, device=dev)
+        sg = None if trace else torch.empty(m, dtype=torch.int8, device=dev)
         st = torch.empty(m, dtype=torch.int32, device=dev)
+        if trace:
+            flags = Q_TRACE | Q_WORLD | (flags & Q_NEAREST)
         query(self.c, poses, flags, fim, met, sg, st, stream)
         return fim, met, sg, st
 

@@ -114,3 +114,76 @@ def test_end_to_end_warehouse_build_and_query(F):
     I_ref, st_ref, *_ = O.query_from_landmarks(sc.landmarks, X.oracle_grid(spec), prm, poses)
     err = X.rel_fro(X.unpack21(fim.cpu().numpy()), I_ref)
     assert err.max() <= X.TAU_F32, err.max()
+
+
+def test_incremental_update_add_and_remove(F):
+    """Sec. VI-A-1: adding or deleting landmarks adds or subtracts their terms.  build(A) then
+    +B equals the oracle field of A u B; then -B returns to the oracle field of A."""
+    sc = X.room_scene()
+    A, Bm = sc.landmarks[:1400], sc.landmarks[1400:]
+    spec = X.ROOM["grid"]
+    field, ws = gpu_build(F, A, spec, 8.0)
+    lmB = torch.from_numpy(np.ascontiguousarray(Bm)).cuda()
+    ws_b = torch.empty(F.build_workspace_bytes(field.c, lmB.shape[0]), dtype=torch.uint8, device="cuda")
+    F.build_update(field.c, lmB, +1, ws_b)
+    torch.cuda.synchronize()
+    ref_all = X.room_field_oracle(True)
+    got = X.unpack_field(field.coeffs.cpu().numpy())
+    assert X.rel_fro(got.reshape(-1, 60, 6), ref_all.reshape(-1, 60, 6)).max() <= X.TAU_F32
+    F.build_update(field.c, lmB, -1, ws_b)
+    torch.cuda.synchronize()
+    ref_A = O.full_field(A, X.oracle_grid(spec), O.make_params(r_max=8.0), about_node=True)
+    got = X.unpack_field(field.coeffs.cpu().numpy())
+    assert X.rel_fro(got.reshape(-1, 60, 6), ref_A.reshape(-1, 60, 6)).max() <= 2 * X.TAU_F32
+    assert F.device_error() == 0
+
+
+def test_update_touches_only_nodes_in_reach(F):
+    """A landmark far outside the lattice reaches no node: the update leaves the field bitwise
+    unchanged; removing a landmark inside changes only nodes within r_max of it."""
+    sc = X.room_scene()
+    spec = X.ROOM["grid"]
+    field, ws = gpu_build(F, sc.landmarks, spec, 3.0)
+    before = field.coeffs.clone()
+    far = torch.tensor([[60.0, 60.0, 60.0]], device="cuda")
+    F.build_update(field.c, far, +1, ws)
+    torch.cuda.synchronize()
+    assert torch.equal(before, field.coeffs)
+    one = torch.from_numpy(sc.landmarks[5:6].copy()).cuda()
+    F.build_update(field.c, one, -1, ws)
+    torch.cuda.synchronize()
+    changed = (before != field.coeffs).any(dim=1).cpu().numpy()
+    n = np.arange(spec.n_nodes)
+    c = np.stack([spec.origin[0] + spec.res * (n % 21), spec.origin[1] + spec.res * ((n // 21) % 21),
+                  spec.origin[2] + spec.res * (n // 441)], axis=1)
+    d = np.linalg.norm(c - sc.landmarks[5].astype(np.float64), axis=1)
+    assert not np.any(changed & (d > 3.0 + 1e-3))
+    assert np.all(changed[(d < 2.9) & (d > 0.2)])
+
+
+def test_trace_factor_field(F):
+    """Sec. VI-A-2: the positional trace factor stores tr(C_k) of the world-frame coefficients
+    (Eq. general_trace_pif), and the query v_r^T C_Tr (Eq. general_trace_query) is the trace of
+    the world-frame FIM."""
+    sc = X.room_scene()
+    spec = X.ROOM["grid"]
+    tf, _ = gpu_build(F, sc.landmarks, spec, 8.0, storage=F.STORAGE_TRACE)
+    got = tf.coeffs.cpu().numpy()
+    assert np.all(got[:, 10:] == 0)
+    Fw = X.room_field_oracle(False)
+    ref = np.trace(Fw, axis1=2, axis2=3)                        # [N, 10]
+    err = np.linalg.norm(got[:, :10] - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert err.max() <= X.TAU_F32, err.max()
+    poses = X.room_poses(1000)
+    _, met, _, st = tf.query(torch.from_numpy(poses).cuda())
+    torch.cuda.synchronize()
+    grid = X.oracle_grid(spec)
+    nodes, w, dw, _ = O.query_cells(grid, poses)
+    I_w = O.query(Fw[nodes], w, poses, O.quad_coeffs(math.pi / 4, 0.5), O.FRAME_WORLD)
+    t_tr, _, _ = X.metric_tolerances(I_w, X.TAU_F32)
+    assert np.all(np.abs(met[:, 0].cpu().numpy() - np.trace(I_w, axis1=1, axis2=2)) <= t_tr)
+    # same as the trace of the full field's world-frame query
+    full, _ = gpu_build(F, sc.landmarks, spec, 8.0)
+    _, met_full, _, _ = full.query(torch.from_numpy(poses).cuda(), F.Q_TRACE | F.Q_WORLD)
+    torch.cuda.synchronize()
+    assert np.all(np.abs(met[:, 0].cpu().numpy() - met_full[:, 0].cpu().numpy()) <= t_tr)
