@@ -43,9 +43,23 @@ WORKLOAD = ("warehouse 50x50x10 m, 200k landmarks (60% box faces / 40% walls, 40
             "(FIM + trace + log|det| + lambda_min)")
 QUERY_BYTES_PER_POSE = 8 * 210 * 4 + 7 * 4 + 21 * 4 + 3 * 8 + 1 + 4   # corners + pose + outputs
 BUILD_FLOPS_PER_PAIR = 151   # shell test 8, rsqrt 1, bearing 4, monomials 31, 66 accumulations 107
+# DRAM traffic of one query launch per pose, from the ncu capture summarised in
+# profiles/query_kernel_warehouse_4M.md (read 28.978 GB + write 0.475 GB for 4,194,304 poses),
+# valid while the kernel sources hash to the recorded digest
+QUERY_TRAFFIC = {"bytes_per_pose": (28.977606e9 + 0.475273e9) / 4194304,
+                 "digest": "eba6f757ea1849e9"}
 SMS = 152
 FP32_LANES = 128
 SM_MAX_MHZ = 2070.0
+
+
+def query_source_digest():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("query.cu", "gather.cuh", "fif_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2008_03324_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def _peaks():
@@ -454,7 +468,10 @@ def main():
                        "l2": "inputs larger than L2: 1.38 GB field gathered at uniform-random positions",
                        "parallelism": f"replicas x{ws}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": None,
+                         "frac": achieved / hbm_peak,
+                         "traffic": (QUERY_TRAFFIC["bytes_per_pose"] * m
+                                     if QUERY_TRAFFIC["digest"] == query_source_digest() else None),
+                         "traffic_note": "ncu dram read+write bytes per launch (profiles/query_kernel_warehouse_4M.md)",
                          "peak_kind": f"{peak_kind} (MEASURED_PEAKS hbm_gbs)",
                          "bytes_per_pose": QUERY_BYTES_PER_POSE, "kernel_ms": kernel_ms},
             "cpu_baseline": cpu,
