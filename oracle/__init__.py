@@ -25,6 +25,7 @@ brute force, invariants and textbook routines).
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -346,3 +347,141 @@ def query_from_landmarks(landmarks, grid: Grid, params: Params, poses, interp=IN
     k = quad_coeffs(params.half_fov, params.v_alpha)
     I = query(corners, w, poses, k, frame)
     return I, st, nodes, w, dw, corners
+
+
+# ---------------------------------------------------------------------------
+# GP visibility (Sec. V-B-2)
+# ---------------------------------------------------------------------------
+
+class _GPStruct(ctypes.Structure):
+    _fields_ = [("axes", _D), ("W", _D), ("ns", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("l", ctypes.c_double), ("ks", ctypes.c_double), ("cos_alpha", ctypes.c_double)]
+
+
+def _gp_sigs():
+    L = lib()
+    if getattr(L, "_gp_ready", False):
+        return L
+    sig = {
+        "or_gp_weights": (ctypes.c_int, [_D, ctypes.c_int, ctypes.c_double, ctypes.c_double, _D]),
+        "or_gp_vp": (None, [_D, ctypes.c_int, _D, ctypes.c_double, ctypes.c_double, _D, _D]),
+        "or_gp_vr": (None, [_D, ctypes.c_int, ctypes.c_double, _D, _D]),
+        "or_gp_visibility": (ctypes.c_double, [_D, ctypes.c_int, _D, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_double, _D, _D]),
+        "or_gp_log_marginal": (ctypes.c_double, [_D, ctypes.c_int, ctypes.c_double, ctypes.c_double, _D,
+                                                 ctypes.c_int]),
+        "or_gp_training": (None, [_D, ctypes.c_int, ctypes.c_double, ctypes.c_double, _D, ctypes.c_int, _D]),
+        "or_field_nodes_gp": (None, [_F, ctypes.c_int64, ctypes.POINTER(Grid), ctypes.POINTER(Params),
+                                     ctypes.POINTER(_GPStruct), _L, ctypes.c_int64, ctypes.c_int, _D]),
+        "or_query_gp_batch": (None, [_D, _D, _D, ctypes.c_int64, ctypes.POINTER(_GPStruct), ctypes.c_int, _D]),
+        "or_pc_fim_gp": (None, [_F, ctypes.c_int64, _D, ctypes.c_int64, ctypes.POINTER(Params),
+                                ctypes.POINTER(_GPStruct), ctypes.c_int, _D]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    L._gp_ready = True
+    return L
+
+
+class GP:
+    """GP visibility model: sample optical axes z_g [ns, 3], SE length scale l, noise variance
+    added to K^s, sigmoid sharpness k_s and half field of view alpha (Eq. sigmoid_vis_func)."""
+
+    def __init__(self, axes, length_scale, noise=1e-10, ks=15.0, half_fov=math.pi / 4):
+        self.axes = np.ascontiguousarray(axes, dtype=np.float64).reshape(-1, 3)
+        self.ns = self.axes.shape[0]
+        self.l, self.noise, self.ks, self.cos_alpha = float(length_scale), float(noise), float(ks), math.cos(half_fov)
+        self.W = np.zeros((self.ns, self.ns))
+        if _gp_sigs().or_gp_weights(_p(self.axes, ctypes.c_double), self.ns, self.l, self.noise,
+                                    _p(self.W, ctypes.c_double)) != 0:
+            raise np.linalg.LinAlgError("singular GP kernel matrix")
+        self.s = _GPStruct(_p(self.axes, ctypes.c_double), _p(self.W, ctypes.c_double), self.ns, 0,
+                           self.l, self.ks, self.cos_alpha)
+
+    def vp(self, p):
+        p = _f64(p)
+        out = np.zeros(self.ns)
+        _gp_sigs().or_gp_vp(_p(self.axes, ctypes.c_double), self.ns, _p(self.W, ctypes.c_double), self.ks,
+                            self.cos_alpha, _p(p, ctypes.c_double), _p(out, ctypes.c_double))
+        return out
+
+    def vr(self, z):
+        z = _f64(z)
+        out = np.zeros(self.ns)
+        _gp_sigs().or_gp_vr(_p(self.axes, ctypes.c_double), self.ns, self.l, _p(z, ctypes.c_double),
+                            _p(out, ctypes.c_double))
+        return out
+
+    def visibility(self, z, p):
+        z, p = _f64(z), _f64(p)
+        return float(_gp_sigs().or_gp_visibility(_p(self.axes, ctypes.c_double), self.ns,
+                                                 _p(self.W, ctypes.c_double), self.l, self.ks, self.cos_alpha,
+                                                 _p(z, ctypes.c_double), _p(p, ctypes.c_double)))
+
+
+def gp_log_marginal(axes, length_scale, noise, Y):
+    axes = np.ascontiguousarray(axes, dtype=np.float64)
+    Y = np.ascontiguousarray(Y, dtype=np.float64)
+    return float(_gp_sigs().or_gp_log_marginal(_p(axes, ctypes.c_double), axes.shape[0], float(length_scale),
+                                               float(noise), _p(Y, ctypes.c_double), Y.shape[0]))
+
+
+def gp_training(axes, ks, half_fov, bearings):
+    axes = np.ascontiguousarray(axes, dtype=np.float64)
+    P = np.ascontiguousarray(bearings, dtype=np.float64).reshape(-1, 3)
+    Y = np.zeros((P.shape[0], axes.shape[0]))
+    _gp_sigs().or_gp_training(_p(axes, ctypes.c_double), axes.shape[0], float(ks), math.cos(half_fov),
+                              _p(P, ctypes.c_double), P.shape[0], _p(Y, ctypes.c_double))
+    return Y
+
+
+def field_nodes_gp(landmarks, grid: Grid, params: Params, gp: GP, nodes, about_node=False,
+                   basis="paper") -> np.ndarray:
+    """[cnt, ns, 6, 6].  basis "paper": C_g = sum_i v_p,i[g] I_i with v_p = W v^s (Eq.
+    general_info_pif with the GP's v_p); basis "sigmoid": D_g = sum_i v^s_g(u_i) I_i, the same
+    sum with W replaced by the identity (so C = W D)."""
+    lm = _f32(landmarks).reshape(-1, 3)
+    nd = np.ascontiguousarray(nodes, dtype=np.int64).reshape(-1)
+    out = np.zeros((nd.shape[0], gp.ns * 36))
+    if basis == "paper":
+        s = gp.s
+    elif basis == "sigmoid":
+        eye = np.eye(gp.ns)
+        s = _GPStruct(_p(gp.axes, ctypes.c_double), _p(eye, ctypes.c_double), gp.ns, 0, gp.l, gp.ks, gp.cos_alpha)
+    else:
+        raise ValueError(basis)
+    _gp_sigs().or_field_nodes_gp(_p(lm, ctypes.c_float), lm.shape[0], ctypes.byref(grid), ctypes.byref(params),
+                                 ctypes.byref(s), _p(nd, ctypes.c_int64), nd.shape[0], int(bool(about_node)),
+                                 _p(out, ctypes.c_double))
+    return out.reshape(-1, gp.ns, 6, 6)
+
+
+def query_gp(corners, w, poses, gp: GP, frame=FRAME_CAMERA) -> np.ndarray:
+    c, ww, ps = _f64(corners), _f64(w), _f64(poses).reshape(-1, 7)
+    out = np.zeros((ps.shape[0], 36))
+    _gp_sigs().or_query_gp_batch(_p(c, ctypes.c_double), _p(ww, ctypes.c_double), _p(ps, ctypes.c_double),
+                                 ps.shape[0], ctypes.byref(gp.s), int(frame), _p(out, ctypes.c_double))
+    return out.reshape(-1, 6, 6)
+
+
+def pc_fim_gp(landmarks, poses, params: Params, gp: GP, frame=FRAME_CAMERA) -> np.ndarray:
+    lm, ps = _f32(landmarks).reshape(-1, 3), _f64(poses).reshape(-1, 7)
+    out = np.zeros((ps.shape[0], 36))
+    _gp_sigs().or_pc_fim_gp(_p(lm, ctypes.c_float), lm.shape[0], _p(ps, ctypes.c_double), ps.shape[0],
+                            ctypes.byref(params), ctypes.byref(gp.s), int(frame), _p(out, ctypes.c_double))
+    return out.reshape(-1, 6, 6)
+
+
+def query_gp_from_landmarks(landmarks, grid: Grid, params: Params, gp: GP, poses, interp=INTERP_TRILINEAR,
+                            frame=FRAME_CAMERA):
+    """GP-field query of poses, the field built on demand at the corner nodes they touch.
+
+    Returns (I [m,6,6], status [m], nodes [m,8], w [m,8])."""
+    nodes, w, _, st = query_cells(grid, poses, interp)
+    uniq, inv = np.unique(nodes.reshape(-1), return_inverse=True)
+    blocks = field_nodes_gp(landmarks, grid, params, gp, uniq, about_node=False)
+    corners = blocks[inv].reshape(nodes.shape[0], 8, gp.ns, 6, 6)
+    I = query_gp(corners, w, poses, gp, frame)
+    return I, st, nodes, w

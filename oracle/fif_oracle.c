@@ -783,3 +783,242 @@ void or_query_grad_batch(const double* corners /*[m][8][360]*/, const double* w 
     for (int64_t i = 0; i < m; ++i)
         grad_one(corners + 2880 * i, w + 8 * i, dw + 24 * i, poses + 7 * i, k, gm + 3 * i, g + 6 * i);
 }
+
+/* ------------------------------------------------------------------------- */
+/* GP visibility (Sec. V-B-2, Eq. sigmoid_vis_func, Eq. gp_vis_approx)         */
+/*                                                                           */
+/*   v_sig(theta) = 1 / (1 + exp(-k_s (cos theta - cos alpha)))                */
+/*   v_gp(z) = K_z (K^s + s_n^2 I)^-1 v^s,  K_z[g] = k(z, z_g),                */
+/*   K^s[g][h] = k(z_g, z_h),  k(a, b) = exp(-|a - b|^2 / (2 l^2))             */
+/* so v_r = K_z and v_p = (K^s + s_n^2 I)^-1 v^s (N_v = N_s).  Readings: the    */
+/* printed Eq. gp_vis_approx omits the inverse of K^s (taken as in Eq.          */
+/* gp_regress); the "noise parameter" s_n^2 is added to the diagonal of K^s;    */
+/* the signal variance of k is 1 (it cancels in the mean).                      */
+/* ------------------------------------------------------------------------- */
+
+static double se_kernel(const double* a, const double* b, double l) {
+    double d0 = a[0] - b[0], d1 = a[1] - b[1], d2 = a[2] - b[2];
+    return exp(-(d0 * d0 + d1 * d1 + d2 * d2) / (2.0 * l * l));
+}
+
+/* W = (K^s + noise I)^-1, [ns][ns], by Gauss-Jordan with partial pivoting */
+int or_gp_weights(const double* axes, int ns, double l, double noise, double* W) {
+    double* A = (double*)malloc(sizeof(double) * (size_t)ns * 2 * ns);
+    if (!A) return -1;
+    for (int i = 0; i < ns; ++i)
+        for (int j = 0; j < 2 * ns; ++j)
+            A[i * 2 * ns + j] = (j < ns) ? se_kernel(axes + 3 * i, axes + 3 * j, l) + (i == j ? noise : 0.0)
+                                         : ((j - ns) == i ? 1.0 : 0.0);
+    int rc = 0;
+    for (int c = 0; c < ns; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < ns; ++r)
+            if (fabs(A[r * 2 * ns + c]) > fabs(A[piv * 2 * ns + c])) piv = r;
+        if (A[piv * 2 * ns + c] == 0.0) { rc = -1; break; }
+        if (piv != c)
+            for (int j = 0; j < 2 * ns; ++j) {
+                double t = A[c * 2 * ns + j]; A[c * 2 * ns + j] = A[piv * 2 * ns + j]; A[piv * 2 * ns + j] = t;
+            }
+        double p = A[c * 2 * ns + c];
+        for (int j = 0; j < 2 * ns; ++j) A[c * 2 * ns + j] /= p;
+        for (int r = 0; r < ns; ++r) {
+            if (r == c) continue;
+            double f = A[r * 2 * ns + c];
+            if (f == 0.0) continue;
+            for (int j = 0; j < 2 * ns; ++j) A[r * 2 * ns + j] -= f * A[c * 2 * ns + j];
+        }
+    }
+    for (int i = 0; i < ns; ++i)
+        for (int j = 0; j < ns; ++j) W[i * ns + j] = A[i * 2 * ns + ns + j];
+    free(A);
+    return rc;
+}
+
+/* v^s: sigmoid visibility of a landmark with unit bearing p at the sample axes */
+static void gp_vs(const double* axes, int ns, double ks, double cos_alpha, const double p[3], double* vs) {
+    for (int g = 0; g < ns; ++g) {
+        double c = axes[3 * g] * p[0] + axes[3 * g + 1] * p[1] + axes[3 * g + 2] * p[2];
+        vs[g] = 1.0 / (1.0 + exp(-ks * (c - cos_alpha)));
+    }
+}
+
+/* v_p = W v^s(p) */
+void or_gp_vp(const double* axes, int ns, const double* W, double ks, double cos_alpha, const double p[3], double* vp) {
+    double vs[512];
+    gp_vs(axes, ns, ks, cos_alpha, p, vs);
+    for (int g = 0; g < ns; ++g) {
+        double s = 0.0;
+        for (int h = 0; h < ns; ++h) s += W[g * ns + h] * vs[h];
+        vp[g] = s;
+    }
+}
+
+/* v_r = K_z */
+void or_gp_vr(const double* axes, int ns, double l, const double z[3], double* vr) {
+    for (int g = 0; g < ns; ++g) vr[g] = se_kernel(z, axes + 3 * g, l);
+}
+
+/* v_gp(z) for a landmark of bearing p: K_z W v^s(p) */
+double or_gp_visibility(const double* axes, int ns, const double* W, double l, double ks, double cos_alpha,
+                        const double z[3], const double p[3]) {
+    double vp[512], vr[512], s = 0.0;
+    or_gp_vp(axes, ns, W, ks, cos_alpha, p, vp);
+    or_gp_vr(axes, ns, l, z, vr);
+    for (int g = 0; g < ns; ++g) s += vr[g] * vp[g];
+    return s;
+}
+
+/* log marginal likelihood of M training vectors y_m over the sample axes (independent GP
+ * draws on the same inputs): sum_m [-1/2 y_m^T K^-1 y_m] - M/2 log|K| - M ns/2 log(2 pi),
+ * K = K^s + noise I (Rasmussen & Williams, Eq. 2.30) */
+double or_gp_log_marginal(const double* axes, int ns, double l, double noise, const double* Y, int M) {
+    double* W = (double*)malloc(sizeof(double) * (size_t)ns * ns);
+    double* K = (double*)malloc(sizeof(double) * (size_t)ns * ns);
+    for (int i = 0; i < ns; ++i)
+        for (int j = 0; j < ns; ++j) K[i * ns + j] = se_kernel(axes + 3 * i, axes + 3 * j, l) + (i == j ? noise : 0.0);
+    or_gp_weights(axes, ns, l, noise, W);
+    /* log det by LU */
+    double lad = 0.0;
+    {
+        double* A = (double*)malloc(sizeof(double) * (size_t)ns * ns);
+        memcpy(A, K, sizeof(double) * (size_t)ns * ns);
+        for (int c = 0; c < ns; ++c) {
+            int piv = c;
+            for (int r = c + 1; r < ns; ++r)
+                if (fabs(A[r * ns + c]) > fabs(A[piv * ns + c])) piv = r;
+            if (piv != c)
+                for (int j = 0; j < ns; ++j) { double t = A[c * ns + j]; A[c * ns + j] = A[piv * ns + j]; A[piv * ns + j] = t; }
+            double p = A[c * ns + c];
+            lad += log(fabs(p));
+            for (int r = c + 1; r < ns; ++r) {
+                double f = A[r * ns + c] / p;
+                for (int j = c; j < ns; ++j) A[r * ns + j] -= f * A[c * ns + j];
+            }
+        }
+        free(A);
+    }
+    double quad = 0.0;
+    for (int m = 0; m < M; ++m) {
+        const double* y = Y + (size_t)m * ns;
+        for (int i = 0; i < ns; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < ns; ++j) s += W[i * ns + j] * y[j];
+            quad += y[i] * s;
+        }
+    }
+    free(W);
+    free(K);
+    return -0.5 * quad - 0.5 * M * lad - 0.5 * M * ns * log(2.0 * M_PI);
+}
+
+/* training vectors for the fit: the sigmoid visibility of landmarks with unit bearings P[m] */
+void or_gp_training(const double* axes, int ns, double ks, double cos_alpha, const double* P, int M, double* Y) {
+    for (int m = 0; m < M; ++m) gp_vs(axes, ns, ks, cos_alpha, P + 3 * m, Y + (size_t)m * ns);
+}
+
+typedef struct {
+    const double* axes;
+    const double* W;
+    int32_t ns;
+    int32_t pad_;
+    double l, ks, cos_alpha;
+} or_gp;
+
+/* Field with GP visibility: C_g(c) = sum_{i in V_c} v_p,i[g] I_i (Eq. general_info_pif with
+ * v_p = W v^s); out [cnt][ns][36] */
+void or_field_nodes_gp(const float* lm, int64_t n, const or_grid* g, const or_params* prm, const or_gp* gp,
+                       const int64_t* nodes, int64_t cnt, int about_node, double* out) {
+    float rmin2 = (float)(prm->r_min * prm->r_min), rmax2 = (float)(prm->r_max * prm->r_max);
+    const double Rid[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    const int ns = gp->ns;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t s = 0; s < cnt; ++s) {
+        int64_t node = nodes[s];
+        int ix = (int)(node % g->nx), iy = (int)((node / g->nx) % g->ny), iz = (int)(node / ((int64_t)g->nx * g->ny));
+        float cf[3] = {node_coord_f32((float)g->origin[0], (float)g->res, ix),
+                       node_coord_f32((float)g->origin[1], (float)g->res, iy),
+                       node_coord_f32((float)g->origin[2], (float)g->res, iz)};
+        double c[3] = {cf[0], cf[1], cf[2]};
+        double o[3] = {0, 0, 0};
+        if (about_node) { o[0] = c[0]; o[1] = c[1]; o[2] = c[2]; }
+        double* C = out + (size_t)36 * ns * s;
+        memset(C, 0, sizeof(double) * 36 * ns);
+        double vp[512];
+        for (int64_t i = 0; i < n; ++i) {
+            const float* pf = lm + 3 * i;
+            if (!or_in_shell_f32(pf, cf, rmin2, rmax2)) continue;
+            double pw[3] = {pf[0], pf[1], pf[2]};
+            double d[3] = {pw[0] - c[0], pw[1] - c[1], pw[2] - c[2]};
+            double nn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            double u[3] = {d[0] / nn, d[1] / nn, d[2] / nn};
+            double J[18], Ii[36];
+            or_gp_vp(gp->axes, ns, gp->W, gp->ks, gp->cos_alpha, u, vp);
+            or_jac_global(pw, Rid, c, o, J);
+            or_fim_gauss(J, prm->sigma, Ii);
+            for (int k = 0; k < ns; ++k)
+                for (int e = 0; e < 36; ++e) C[36 * k + e] += vp[k] * Ii[e];
+        }
+    }
+}
+
+/* Query with GP visibility from world-frame corner sets [m][8][ns][36] */
+void or_query_gp_batch(const double* corners, const double* w, const double* poses, int64_t m, const or_gp* gp,
+                       int frame, double* out) {
+    const int ns = gp->ns;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < m; ++i) {
+        const double* pose = poses + 7 * i;
+        double q[4] = {pose[3], pose[4], pose[5], pose[6]}, R[9], t[3] = {pose[0], pose[1], pose[2]};
+        or_quat_to_rot(q, R);
+        double z[3] = {R[2], R[5], R[8]}, vr[512];
+        or_gp_vr(gp->axes, ns, gp->l, z, vr);
+        double Iw[36];
+        memset(Iw, 0, sizeof(Iw));
+        for (int j = 0; j < 8; ++j) {
+            double wj = w[8 * i + j];
+            if (wj == 0.0) continue;
+            const double* Cj = corners + ((size_t)i * 8 + j) * 36 * ns;
+            for (int k = 0; k < ns; ++k)
+                for (int e = 0; e < 36; ++e) Iw[e] += vr[k] * wj * Cj[36 * k + e];
+        }
+        double* I = out + 36 * i;
+        if (frame == OR_FRAME_WORLD) { memcpy(I, Iw, sizeof(Iw)); continue; }
+        double Ad[36], AdT[36], tmp[36];
+        adjoint_se3(R, t, Ad);
+        transpose(Ad, AdT, 6, 6);
+        matmul(AdT, Iw, tmp, 6, 6, 6);
+        matmul(tmp, Ad, I, 6, 6, 6);
+    }
+}
+
+/* Point-cloud FIM weighted by the GP visibility of each landmark (what the GP field reproduces
+ * at a node): sum_i v_gp(z; u_i) I_i over the range shell around t */
+void or_pc_fim_gp(const float* lm, int64_t n, const double* poses, int64_t m, const or_params* prm, const or_gp* gp,
+                  int frame, double* out) {
+    float rmin2 = (float)(prm->r_min * prm->r_min), rmax2 = (float)(prm->r_max * prm->r_max);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t j = 0; j < m; ++j) {
+        const double* pose = poses + 7 * j;
+        double q[4] = {pose[3], pose[4], pose[5], pose[6]}, R[9], t[3] = {pose[0], pose[1], pose[2]};
+        double o[3] = {0, 0, 0};
+        or_quat_to_rot(q, R);
+        double z[3] = {R[2], R[5], R[8]};
+        float tf[3] = {(float)t[0], (float)t[1], (float)t[2]};
+        double* I = out + 36 * j;
+        memset(I, 0, 36 * sizeof(double));
+        for (int64_t i = 0; i < n; ++i) {
+            const float* pf = lm + 3 * i;
+            if (!or_in_shell_f32(pf, tf, rmin2, rmax2)) continue;
+            double pw[3] = {pf[0], pf[1], pf[2]};
+            double d[3] = {pw[0] - t[0], pw[1] - t[1], pw[2] - t[2]};
+            double nn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            double u[3] = {d[0] / nn, d[1] / nn, d[2] / nn};
+            double v = or_gp_visibility(gp->axes, gp->ns, gp->W, gp->l, gp->ks, gp->cos_alpha, z, u);
+            double J[18], Ii[36];
+            if (frame == OR_FRAME_CAMERA) or_jac_local(pw, R, t, J);
+            else or_jac_global(pw, R, t, o, J);
+            or_fim_gauss(J, prm->sigma, Ii);
+            for (int e = 0; e < 36; ++e) I[e] += v * Ii[e];
+        }
+    }
+}

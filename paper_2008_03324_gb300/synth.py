@@ -383,6 +383,22 @@ def horizontal_quats(yaw) -> np.ndarray:
     return rot_to_quat(look_rotation(np.asarray(yaw).reshape(-1), np.zeros(np.size(yaw))))
 
 
+def fibonacci_sphere(n: int) -> np.ndarray:
+    """n nearly uniform unit vectors (spherical Fibonacci lattice), [n, 3] float64: the sample
+    optical axes of the GP visibility model."""
+    i = np.arange(n, dtype=np.float64) + 0.5
+    z = 1.0 - 2.0 * i / n
+    r = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    phi = i * math.pi * (3.0 - math.sqrt(5.0))
+    return np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1)
+
+
+def sphere_points(seed: int, m: int) -> np.ndarray:
+    """m uniform unit vectors (normalised 3-D Gaussian), [m, 3] float64."""
+    v = _rng(seed).standard_normal((m, 3))
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
 # ---------------------------------------------------------------------------
 # named workloads
 # ---------------------------------------------------------------------------
