@@ -70,6 +70,9 @@ typedef struct CUstream_st* fif_stream_t;
 /* ---- storage of the field ------------------------------------------------------------ */
 #define FIF_STORAGE_F32 0    /* float32, 216 elements (864 B) per node                  */
 #define FIF_STORAGE_BF16 1   /* bfloat16 (round to nearest even), 224 elements (448 B)    */
+#define FIF_STORAGE_GP 3     /* GP visibility (Sec. V-B-2): float32, per node the 21 x N_s  */
+                             /* matrix of D_g (see fif_gp), entry e of D_g at e*rs + g with  */
+                             /* rs = fif_gp_row_stride(N_s); fif_gp_stride(N_s) per node     */
 #define FIF_STORAGE_TRACE 2  /* the positional trace factor of Sec. VI-A-2 (Eq.             */
                              /* general_trace_pif): float32 tr(C_k^world), k = 0..9, plus 2 */
                              /* zero pads = 12 elements (48 B) per node; fif_query then      */
@@ -123,6 +126,30 @@ typedef struct fif_pinhole {
     int32_t width, height;
 } fif_pinhole;
 
+/* GP visibility model (Sec. V-B-2, Eq. sigmoid_vis_func, Eq. gp_vis_approx).  The visibility of
+ * a landmark with unit bearing u seen along the optical axis z is the GP regression mean
+ *   v_gp(z) = K_z (K^s + noise_var I)^-1 v^s(u),
+ *   v^s_g(u) = 1 / (1 + exp(-k_s (z_g . u - cos alpha)))   (the sigmoid visibility at axis z_g),
+ *   K_z[g] = exp(-|z - z_g|^2 / (2 l^2)),  K^s[g][h] = exp(-|z_g - z_h|^2 / (2 l^2)),
+ * over N_s sample optical axes z_g (the printed Eq. gp_vis_approx omits the inverse of K^s; it
+ * is read as in Eq. gp_regress).  alpha is params.half_fov.
+ * Storage: a GP field keeps, per node, D_g = sum_i v^s_g(u_i) I_i (every weight in (0, 1); I_i
+ * about the node as for the quadratic field) and the query applies the kriging weights
+ *   a(z) = (K^s + noise_var I)^-1 K_z^T   (double-precision kernel values, compensated sums),
+ *   I = sum_g a_g(z) D_g = K_z (K^s + noise_var I)^-1 D = V_I C_I of Eq. fim_separation.
+ * The paper's C_I = (K^s)^-1 D is never stored: its entries grow with the condition number of
+ * K^s, and single-precision storage of them loses up to four digits in the query. */
+#define FIF_GP_MAX_SAMPLES 96
+typedef struct fif_gp {
+    int32_t n_samples;                      /* N_s, 1 .. FIF_GP_MAX_SAMPLES                  */
+    int32_t reserved;
+    double length_scale;                    /* l                                              */
+    double noise_var;                       /* added to the diagonal of K^s (paper: 1e-10)    */
+    double k_s;                             /* sigmoid sharpness (paper: 15)                  */
+    double axes[FIF_GP_MAX_SAMPLES][3];     /* sample optical axes z_g (normalised on upload) */
+    void* d_aux;                            /* device buffer filled by fif_gp_upload           */
+} fif_gp;
+
 /* A field: the lattice, the method's parameters and the caller-owned device storage.
  * Storage layout: node n occupies elements [n*stride, (n+1)*stride) of `coeffs`; element
  * n*stride + 21*k + e holds entry e (upper-triangular, row-major) of the 6x6 matrix
@@ -137,11 +164,12 @@ typedef struct fif_pinhole {
 typedef struct fif_field {
     fif_grid grid;
     fif_params params;
-    int32_t storage;   /* FIF_STORAGE_F32 or FIF_STORAGE_BF16                      */
+    int32_t storage;   /* FIF_STORAGE_*                                              */
     int32_t stride;    /* elements per node                                         */
     void* coeffs;      /* device storage, caller-owned                              */
     size_t bytes;      /* size of `coeffs` in bytes                                 */
     double k[3];       /* k0, k1, k2                                                */
+    fif_gp gp;         /* GP model (FIF_STORAGE_GP only)                             */
 } fif_field;
 
 /* Library version (major*10000 + minor*100 + patch). */
@@ -150,7 +178,8 @@ FIF_API int32_t fif_version(void);
 /* Static name of a return code. */
 FIF_API const char* fif_status_str(int32_t code);
 
-/* Bytes of field storage for `grid` with the given storage type (0 on a bad argument). */
+/* Bytes of field storage for `grid` with the given storage type (0 on a bad argument; for
+ * FIF_STORAGE_GP use fif_gp_field_bytes). */
 FIF_API size_t fif_field_bytes(const fif_grid* grid, int32_t storage);
 
 /* Fill *field: validate grid and params, solve (k0, k1, k2) from Eq. quadratic_conditions
@@ -158,6 +187,44 @@ FIF_API size_t fif_field_bytes(const fif_grid* grid, int32_t storage);
  * (at least fif_field_bytes()).  Host only; does not touch the storage. */
 FIF_API int32_t fif_field_init(fif_field* field, const fif_grid* grid, const fif_params* params,
                        int32_t storage, void* d_coeffs, size_t bytes);
+
+/* Row stride rs of a GP node record: the smallest count >= n_samples that is 2 more than a
+ * multiple of 4 (0 on a bad count).  Entry e of D_g sits at e*rs + g; pads are zero. */
+FIF_API int32_t fif_gp_row_stride(int32_t n_samples);
+
+/* Elements per node of a GP field: 21 rs rounded up to a multiple of 4 (16-byte records). */
+FIF_API int32_t fif_gp_stride(int32_t n_samples);
+
+/* Bytes of the GP model's device buffer d_aux. */
+FIF_API size_t fif_gp_aux_bytes(int32_t n_samples);
+
+/* Prepare the model for device use: normalise the axes, compute W = (K^s + noise_var I)^-1 on
+ * the host in double precision (Cholesky factorisation, then the inverse from the factor),
+ * and copy W (split into single-precision high and low parts) and the axes into the caller's
+ * device buffer d_aux (bytes >= fif_gp_aux_bytes(n_samples)); sets gp->d_aux.  Synchronises
+ * `stream`.  FIF_EINVAL on a bad count, axis, length scale, noise or k_s, or when
+ * K^s + noise_var I is not positive definite in double precision. */
+FIF_API int32_t fif_gp_upload(fif_gp* gp, void* d_aux, size_t bytes, fif_stream_t stream);
+
+/* Length scale by maximum marginal likelihood (Sec. V-B-2; Rasmussen and Williams Eq. 2.30):
+ * training vectors y_m = v^s(p_m) for m unit bearings p_m (host double [m][3]) at the N_s
+ * axes of gp, independent draws, maximise over l in [l_lo, l_hi]
+ *   L(l) = sum_m -1/2 y_m^T (K^s_l + noise_var I)^-1 y_m - m/2 log|K^s_l + noise_var I|
+ * by a scan of 97 log-spaced points, then golden-section refinement of the best bracket to a
+ * relative width of 1e-7.  Host only, double precision (Cholesky).  gp->length_scale is
+ * ignored; the maximiser is written to *l_out. */
+FIF_API int32_t fif_gp_fit_length_scale(const fif_gp* gp, double half_fov, const double* bearings, int32_t m,
+                                        double l_lo, double l_hi, double* l_out);
+
+/* Bytes of GP field storage for `grid` and n_samples axes (0 on a bad argument). */
+FIF_API size_t fif_gp_field_bytes(const fif_grid* grid, int32_t n_samples);
+
+/* fif_field_init for a GP field (storage FIF_STORAGE_GP): gp must have been uploaded
+ * (fif_gp_upload); the field keeps a copy of the struct, and gp->d_aux must stay valid while
+ * the field is used.  params.v_alpha is unused.  fif_build, fif_build_update and fif_query
+ * accept the field; fif_query_backward, fif_field_save and fif_build_static return FIF_EINVAL. */
+FIF_API int32_t fif_field_init_gp(fif_field* field, const fif_grid* grid, const fif_params* params,
+                                  const fif_gp* gp, void* d_coeffs, size_t bytes);
 
 /* Bytes of device workspace fif_build() needs for n landmarks (0 on a bad argument). */
 FIF_API size_t fif_build_workspace_bytes(const fif_field* field, int64_t n_landmarks);
@@ -168,7 +235,10 @@ FIF_API size_t fif_build_workspace_bytes(const fif_field* field, int64_t n_landm
  * fif_build_workspace_bytes(field, n) bytes, contents on entry ignored.  Sums are taken
  * in single precision with compensated (Kahan) accumulation over blocks of landmarks;
  * the summation order is fixed by the input order, so equal inputs give bitwise equal
- * fields.  Overwrites the whole storage.  n may be 0 (the field becomes zero). */
+ * fields.  Overwrites the whole storage.  n may be 0 (the field becomes zero).
+ * GP field (FIF_STORAGE_GP): the same reduction with weights v^s_g(u_i) gives D_g for every
+ * sample axis g (single-precision bearings and sigmoid: ex2 / rcp approximations, relative
+ * error of each weight below 3e-6). */
 FIF_API int32_t fif_build(fif_field* field, const float* d_landmarks, int64_t n, void* d_workspace,
                   size_t workspace_bytes, fif_stream_t stream);
 
@@ -215,7 +285,11 @@ FIF_API int32_t fif_build_static(fif_field* field, const float* d_landmarks, int
  * Trace is summed in single precision; log|det| comes from a double-precision LDL^T
  * (LU with pivoting when it breaks down) of the FIM, and lambda_min from a
  * single-precision Jacobi eigenvector refined by a double-precision Rayleigh quotient.
- * Positions outside the lattice are clamped onto it. */
+ * Positions outside the lattice are clamped onto it.  m = 0 returns FIF_OK and touches nothing
+ * (every pointer may then be NULL).
+ * GP field (FIF_STORAGE_GP): I(T) = sum_g a_g(z) D_g(t) with the kriging weights
+ *   a(z) = (K^s + noise_var I)^-1 K_z^T (K_z in double precision, the product as compensated
+ *   single-precision sums with W split into high and low parts), D_g interpolated as above. */
 FIF_API int32_t fif_query(const fif_field* field, const float* d_poses, int64_t m, int32_t flags,
                   float* d_fim, double* d_metrics, int8_t* d_sign, int32_t* d_status,
                   fif_stream_t stream);

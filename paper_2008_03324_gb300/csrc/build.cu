@@ -27,6 +27,7 @@
 // epilogue expands the 66 moments into the 210 stored coefficients.
 #include "fif_common.cuh"
 #include "fif_internal.h"
+#include "landmark_stream.cuh"
 
 #include <cmath>
 #include <cstring>
@@ -248,14 +249,6 @@ __device__ float coef_local(const float* hs, const float* ls, int tid, int k, in
     return v;
 }
 
-__device__ __forceinline__ void kahan_merge(float* hs, float* ls, int idx, float x) {
-    const float s = hs[idx], c = ls[idx];
-    const float y = x - c;
-    const float t = s + y;
-    ls[idx] = (t - s) - y;
-    hs[idx] = t;
-}
-
 __global__ void __launch_bounds__(kThreads, 2) build_kernel(BuildArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     BuildSmem& S = *reinterpret_cast<BuildSmem*>(smem_raw);
@@ -294,35 +287,8 @@ __global__ void __launch_bounds__(kThreads, 2) build_kernel(BuildArgs a) {
     // ---- enumerate candidate runs: one bin row (y, z) per entry ----
     const BinGrid& bg = a.bg;
     const float rc = a.rcull, rc2 = rc * rc;
-    const int ry0 = max(0, (int)floorf((blo[1] - rc - bg.lo[1]) * bg.inv_size));
-    const int ry1 = min(bg.n[1] - 1, (int)floorf((bhi[1] + rc - bg.lo[1]) * bg.inv_size));
-    const int rz0 = max(0, (int)floorf((blo[2] - rc - bg.lo[2]) * bg.inv_size));
-    const int rz1 = min(bg.n[2] - 1, (int)floorf((bhi[2] + rc - bg.lo[2]) * bg.inv_size));
-    const int nry = max(0, ry1 - ry0 + 1), nrz = max(0, rz1 - rz0 + 1);
-    // the host sizes bins so a brick never touches more than kMaxRuns rows; if that ever
-    // failed the field would be wrong, so report it instead of truncating silently
-    if (nry * nrz > kMaxRuns && tid == 0) set_error(a.err, FIF_ERANGE);
-    const int nrows = min(nry * nrz, kMaxRuns);
     const int* startp = reinterpret_cast<const int*>(a.ws + a.lay.start);
-    for (int r = tid; r < nrows; r += kThreads) {
-        const int ry = ry0 + r % nry, rz = rz0 + r / nry;
-        const float ylo = bg.lo[1] + ry * bg.size, yhi = ylo + bg.size;
-        const float zlo = bg.lo[2] + rz * bg.size, zhi = zlo + bg.size;
-        const float dy = fmaxf(0.f, fmaxf(ylo - bhi[1], blo[1] - yhi));
-        const float dz = fmaxf(0.f, fmaxf(zlo - bhi[2], blo[2] - zhi));
-        const float d2 = dy * dy + dz * dz;
-        int2 run = make_int2(0, 0);
-        if (d2 <= rc2) {
-            const float rx = sqrtf(rc2 - d2);
-            const int bx0 = max(0, (int)floorf((blo[0] - rx - bg.lo[0]) * bg.inv_size));
-            const int bx1 = min(bg.n[0] - 1, (int)floorf((bhi[0] + rx - bg.lo[0]) * bg.inv_size));
-            if (bx1 >= bx0) {
-                const int rowb = bg.n[0] * (ry + bg.n[1] * rz);
-                run = make_int2(startp[rowb + bx0], startp[rowb + bx1 + 1]);
-            }
-        }
-        S.runs[r] = run;
-    }
+    const int nrows = enumerate_runs(bg, startp, blo, bhi, rc, S.runs, kMaxRuns, tid, kThreads, a.err);
     if (tid == 0) {
         S.nruns = nrows;
         for (int s = 0; s < kSlots; ++s) mbar_init(&S.bars[s], 1);
@@ -332,30 +298,10 @@ __global__ void __launch_bounds__(kThreads, 2) build_kernel(BuildArgs a) {
 
     // ---- producer state (thread 0 only) ----
     const float4* sorted = reinterpret_cast<const float4*>(a.ws + a.lay.sorted);
-    int prod_run = 0, prod_off = 0;
+    TileProducer<kTile> prod;
     auto produce = [&](int slot) {
-        // fill one tile from the run list; an empty tile marks the end
-        uint64_t* bar = &S.bars[slot];
-        int cnt = 0;
-        while (cnt < kTile && prod_run < S.nruns) {
-            const int2 run = S.runs[prod_run];
-            const int s0 = run.x + prod_off;
-            const int take = min(run.y - s0, kTile - cnt);
-            if (take > 0) {
-                asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)),
-                             "r"((uint32_t)take * 16u)
-                             : "memory");
-                bulk_g2s(&S.tile[slot][cnt], sorted + s0, (uint32_t)take * 16u, bar);
-                cnt += take;
-                prod_off += take;
-            }
-            if (run.x + prod_off >= run.y) {
-                ++prod_run;
-                prod_off = 0;
-            }
-        }
-        S.tile_count[slot] = cnt;
-        mbar_arrive(bar);
+        S.tile_count[slot] = prod.fill(S.tile[slot], S.runs, S.nruns, sorted, &S.bars[slot]);
+        mbar_arrive(&S.bars[slot]);
     };
     if (tid == 0) {
         fence_proxy_async();
@@ -603,7 +549,7 @@ BuildLayout build_layout(const BinGrid& bg, int64_t n) {
     return L;
 }
 
-int launch_build(const BuildArgs& a, cudaStream_t stream) {
+int launch_binning(const BuildArgs& a, cudaStream_t stream) {
     const int64_t nb = (int64_t)a.bg.n[0] * a.bg.n[1] * a.bg.n[2];
     if (nb > (int64_t)INT32_MAX - 1 || a.n > (int64_t)INT32_MAX) return FIF_ERANGE;
     int* count = reinterpret_cast<int*>(a.ws + a.lay.count);
@@ -621,6 +567,13 @@ int launch_build(const BuildArgs& a, cudaStream_t stream) {
         bin_scatter_kernel<<<blocks(a.n), T, 0, stream>>>(a.landmarks, a.n, binof, start, count, sorted);
         bin_sort_kernel<<<blocks(nb), T, 0, stream>>>(sorted, start, (int)nb);
     }
+    return cudaPeekAtLastError() == cudaSuccess ? FIF_OK : FIF_ECUDA;
+}
+
+int launch_build(const BuildArgs& a, cudaStream_t stream) {
+    if (a.storage == FIF_STORAGE_GP) return launch_gp_build(a, stream);
+    const int rc = launch_binning(a, stream);
+    if (rc != FIF_OK) return rc;
     const int smem = (int)sizeof(BuildSmem);
     if (cudaFuncSetAttribute(build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return FIF_ECUDA;

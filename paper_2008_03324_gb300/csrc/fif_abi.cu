@@ -55,15 +55,34 @@ int check_params(const fif_params* p) {
     return FIF_OK;
 }
 
+int check_gp(const fif_gp* gp) {
+    if (gp->n_samples < 1 || gp->n_samples > FIF_GP_MAX_SAMPLES || !gp->d_aux) return FIF_EINVAL;
+    if (!(gp->length_scale > 0.0) || !std::isfinite(gp->length_scale)) return FIF_EINVAL;
+    if (!(gp->k_s > 0.0) || !std::isfinite(gp->k_s)) return FIF_EINVAL;
+    if (reinterpret_cast<uintptr_t>(gp->d_aux) & 255u) return FIF_EALIGN;
+    return FIF_OK;
+}
+
+// storage bytes a field of this kind needs
+size_t field_need(const fif_field* f) {
+    return f->storage == FIF_STORAGE_GP ? fif_gp_field_bytes(&f->grid, f->gp.n_samples)
+                                        : fif_field_bytes(&f->grid, f->storage);
+}
+
 int check_field(const fif_field* f) {
     if (!f) return FIF_EINVAL;
     int rc = check_grid(&f->grid);
     if (rc) return rc;
     if ((rc = check_params(&f->params))) return rc;
-    if (stride_of(f->storage) == 0 || f->stride != stride_of(f->storage)) return FIF_EINVAL;
+    if (f->storage == FIF_STORAGE_GP) {
+        if ((rc = check_gp(&f->gp))) return rc;
+        if (f->stride != fif_gp_stride(f->gp.n_samples)) return FIF_EINVAL;
+    } else if (stride_of(f->storage) == 0 || f->stride != stride_of(f->storage)) {
+        return FIF_EINVAL;
+    }
     if (!f->coeffs) return FIF_EINVAL;
     if (!aligned16(f->coeffs)) return FIF_EALIGN;
-    if (f->bytes < fif_field_bytes(&f->grid, f->storage)) return FIF_ESIZE;
+    if (f->bytes < field_need(f)) return FIF_ESIZE;
     return FIF_OK;
 }
 
@@ -161,6 +180,27 @@ int32_t fif_field_init(fif_field* field, const fif_grid* grid, const fif_params*
     return FIF_OK;
 }
 
+int32_t fif_field_init_gp(fif_field* field, const fif_grid* grid, const fif_params* params, const fif_gp* gp,
+                          void* d_coeffs, size_t bytes) {
+    if (!field || !gp) return FIF_EINVAL;
+    int rc = check_grid(grid);
+    if (rc) return rc;
+    if ((rc = check_params(params))) return rc;
+    if ((rc = check_gp(gp))) return rc;
+    if (!d_coeffs) return FIF_EINVAL;
+    if (!aligned16(d_coeffs)) return FIF_EALIGN;
+    if (bytes < fif_gp_field_bytes(grid, gp->n_samples)) return FIF_ESIZE;
+    std::memset(field, 0, sizeof(*field));
+    field->grid = *grid;
+    field->params = *params;
+    field->storage = FIF_STORAGE_GP;
+    field->stride = fif_gp_stride(gp->n_samples);
+    field->coeffs = d_coeffs;
+    field->bytes = bytes;
+    field->gp = *gp;
+    return FIF_OK;
+}
+
 size_t fif_build_workspace_bytes(const fif_field* field, int64_t n) {
     if (check_field(field) || n < 0) return 0;
     const fif::BinGrid bg = fif::make_bin_grid(field);
@@ -208,6 +248,16 @@ static int32_t build_impl(fif_field* field, const float* d_landmarks, int64_t n,
     a.out = field->coeffs;
     a.err = device_error_ptr();
     a.accumulate = accumulate;
+    if (field->storage == FIF_STORAGE_GP) {
+        const fif_gp& gp = field->gp;
+        const fif::GpAuxLayout L = fif::gp_aux_layout(gp.n_samples, fif_gp_row_stride(gp.n_samples));
+        a.gp_axes = reinterpret_cast<const float4*>(static_cast<const unsigned char*>(gp.d_aux) + L.axes_f);
+        a.gp_ns = gp.n_samples;
+        a.gp_rs = fif_gp_row_stride(gp.n_samples);
+        const double log2e = 1.4426950408889634;
+        a.gp_scale = (float)(gp.k_s * log2e);
+        a.gp_shift = (float)(gp.k_s * log2e * std::cos(field->params.half_fov));
+    }
     return fif::launch_build(a, stream);
 }
 
@@ -217,8 +267,8 @@ int32_t fif_query(const fif_field* field, const float* d_poses, int64_t m, int32
     if (rc) return rc;
     if (m < 0 || (m > 0 && !d_poses)) return FIF_EINVAL;
     if (flags & ~(FIF_Q_NEAREST | FIF_Q_WORLD | FIF_Q_METRICS)) return FIF_EINVAL;
+    if (m == 0) return FIF_OK;   // nothing to write (empty buffers may be NULL)
     if ((flags & FIF_Q_METRICS) && !d_metrics && !d_sign && !d_status) return FIF_EINVAL;
-    if (m == 0) return FIF_OK;
     if (reinterpret_cast<uintptr_t>(d_poses) & 3u) return FIF_EALIGN;
     fif::QueryArgs a = query_args(field, d_poses, m, flags);
     a.fim = d_fim;
@@ -229,6 +279,17 @@ int32_t fif_query(const fif_field* field, const float* d_poses, int64_t m, int32
         // the trace factor answers only the world-frame trace (Eq. general_trace_query)
         if ((flags & FIF_Q_METRICS) != FIF_Q_TRACE || !(flags & FIF_Q_WORLD) || d_fim || d_sign) return FIF_EINVAL;
         return fif::launch_trace_query(a, stream);
+    }
+    if (field->storage == FIF_STORAGE_GP) {
+        const fif_gp& gp = field->gp;
+        a.gp_ns = gp.n_samples;
+        a.gp_rs = fif_gp_row_stride(gp.n_samples);
+        const fif::GpAuxLayout L = fif::gp_aux_layout(a.gp_ns, a.gp_rs);
+        const unsigned char* aux = static_cast<const unsigned char*>(gp.d_aux);
+        a.gp_axes = reinterpret_cast<const double*>(aux + L.axes_d);
+        a.gp_wt = reinterpret_cast<const float2*>(aux + L.wt);
+        a.gp_inv2l2 = 1.0 / (2.0 * gp.length_scale * gp.length_scale);
+        return fif::launch_gp_query(a, stream);
     }
     return fif::launch_query(a, stream);
 }
@@ -288,6 +349,7 @@ int32_t fif_pointcloud_fim(const float* d_landmarks, int64_t n, const fif_params
 int32_t fif_field_save(const fif_field* field, const char* path, void* host_staging, fif_stream_t stream) {
     int rc = check_field(field);
     if (rc) return rc;
+    if (field->storage == FIF_STORAGE_GP) return FIF_EINVAL;   // the file format has no GP model
     if (!path) return FIF_EINVAL;
     const size_t bytes = fif_field_bytes(&field->grid, field->storage);
     unsigned char* buf = static_cast<unsigned char*>(host_staging);

@@ -26,8 +26,14 @@ struct QueryArgs {
     int8_t* sign;
     int32_t* status;
     int* err;
+    // GP visibility field (storage FIF_STORAGE_GP)
+    int gp_ns, gp_rs;
+    const double* gp_axes;     // [ns][4] (x, y, z, 0)
+    const float2* gp_wt;       // [ns][rs]: (high, low) single-precision parts of W[g][h] at h * rs + g
+    double gp_inv2l2;          // 1 / (2 l^2)
 };
 int launch_query(const QueryArgs& a, cudaStream_t stream);
+int launch_gp_query(const QueryArgs& a, cudaStream_t stream);
 int launch_trace_query(const QueryArgs& a, cudaStream_t stream);
 
 // ---- query adjoint -------------------------------------------------------------------
@@ -83,8 +89,25 @@ struct BuildArgs {
     void* out;
     int* err;
     int accumulate;   // 0: overwrite the field; +1 / -1: add / subtract these landmarks' share
+    // GP visibility field (storage FIF_STORAGE_GP): v^s_g = 1 / (1 + 2^(gp_shift - gp_scale z_g.u))
+    const float4* gp_axes;    // [ns] (x, y, z, 0)
+    int gp_ns, gp_rs;
+    float gp_scale;           // k_s log2(e)
+    float gp_shift;           // k_s log2(e) cos(alpha)
 };
 int launch_build(const BuildArgs& a, cudaStream_t stream);
+// counting sort of the landmarks into the bins of a.bg (fills the workspace layout a.lay)
+int launch_binning(const BuildArgs& a, cudaStream_t stream);
+int launch_gp_build(const BuildArgs& a, cudaStream_t stream);
+
+// GP model buffer (fif_gp.d_aux): offsets in bytes
+struct GpAuxLayout {
+    size_t axes_f;   // float4[ns]
+    size_t axes_d;   // double[ns][4]
+    size_t wt;       // float2[ns][rs]
+    size_t total;
+};
+GpAuxLayout gp_aux_layout(int ns, int rs);
 
 // ---- point cloud ---------------------------------------------------------------------
 struct PointCloudArgs {

@@ -1,0 +1,723 @@
+// gp.cu -- Fisher Information Field with GP visibility (Sec. V-B-2 of the paper): build and
+// query kernels for sm_103a.
+//
+// The GP visibility of a landmark with bearing u seen along optical axis z is
+//   v_gp(z) = K_z (K^s + s_n^2 I)^-1 v^s(u),   v^s_g(u) = 1 / (1 + exp(-k_s (z_g . u - cos a))),
+// so the field is separable with N_v = N_s (Eq. gp_vis_approx, Eq. fim_separation).  The
+// field stores, per node c and sample axis g, the 6x6
+//   D_g(c) = sum_{i in shell(c)} v^s_g(u_i) I_i        (I_i about the node, as in build.cu)
+// and the query contracts it with the kriging weights a(z) = (K^s + s_n^2 I)^-1 K_z^T:
+//   I(T) = sum_g a_g(z) D_g(t),  which equals K_z C_I with the paper's C_I = (K^s)^-1 D.
+// Storing D instead of C_I keeps every stored weight in (0, 1); the ill-conditioning of K^s
+// then sits in a(z) alone, which the query evaluates with double-precision kernel values and
+// compensated single-precision sums.
+//
+// Node record (float32): entry e (upper-triangular 6x6, row-major) of D_g at e * rs + g,
+// rs = fif_gp_row_stride(N_s) (rs = 2 mod 4: a lane per entry e reading 8-byte pairs hits
+// distinct banks), zero pads, stride = 21 rs rounded up to 4 floats.
+//
+// Build (gp_build_kernel): one CTA per 4 x 2 x 2 brick of nodes, one warp per node.  The
+// brick's candidate landmarks stream through a ring of shared-memory tiles (landmark_stream);
+// each warp takes the exact single-precision shell decision for its node 32 landmarks at a
+// time, compacts the in-shell ones (u, 1/n) into a list, and every lane then accumulates, for
+// its sample axes g = lane + 32 k, the 15 moments
+//   sum v_g u_a u_b,  sum v_g u_a u_b / n^2,  sum v_g u_a / n
+// from which all 21 entries of D_g follow (|u| = 1: 1 - u_a^2 = u_b^2 + u_c^2).  Blocks of
+// about 64 pairs are summed in registers and merged into Kahan pairs in shared memory.
+//
+// Query (gp_query_kernel): a persistent CTA walks groups of 32 poses with three warp roles:
+//  weights  (4 warps)  K_z in double precision, a(z) = W K_z as compensated single-precision
+//                      sums with W split into high and low parts (two-product / two-sum);
+//  contract (8 warps)  warp j streams corner j of each pose (one bulk copy of the node record
+//                      into its own ring), lane e < 21 forms w_j sum_g a_g D_g[e];
+//  metric   (1 warp)   lane = pose: moves the 8 corner matrices from their nodes to the
+//                      camera position, sums, rotates into the camera frame, and reduces to
+//                      trace / log|det| / lambda_min as the quadratic query does.
+#include "fif_common.cuh"
+#include "fif_internal.h"
+#include "landmark_stream.cuh"
+
+#include <cmath>
+#include <cstring>
+
+namespace fif {
+
+namespace {
+
+// ------------------------------------------------------------------------------------
+// build
+// ------------------------------------------------------------------------------------
+constexpr int kGbWarps = 16;                   // a 4 x 2 x 2 brick of nodes, one warp each
+constexpr int kGbThreads = kGbWarps * 32;
+constexpr int kGbTile = 256;
+constexpr int kGbSlots = 3;
+constexpr int kGbBlock = 64;                   // pairs per register block (Kahan granularity)
+constexpr int kGbMaxRuns = 2048;
+constexpr int kGbMom = 15;
+
+template <int G>
+struct GpBuildSmem {
+    float hi[kGbWarps][kGbMom * G][32];
+    float lo[kGbWarps][kGbMom * G][32];
+    float4 tile[kGbSlots][kGbTile];
+    float4 list[kGbWarps][32];
+    int2 runs[kGbMaxRuns];
+    int tile_count[kGbSlots];
+    int nruns;
+    uint64_t bars[kGbSlots];
+};
+
+FIF_DEV float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+FIF_DEV float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// entry e of D_g from its 15 moments m (before 1/sigma^2):
+//   TT = P/n^2, TR = -[u]x / n, RR = P with P = I - u u^T; m[0..5] = sum v (xx yy zz xy xz yz),
+//   m[6..11] the same over n^2, m[12..14] = sum v (x y z) / n
+FIF_DEV float gp_entry(int e, const float* m) {
+    const int r = sym_row(e), c = sym_col(e);
+    auto diag = [&](int base, int a) {
+        return a == 0 ? m[base + 1] + m[base + 2] : a == 1 ? m[base + 0] + m[base + 2] : m[base + 0] + m[base + 1];
+    };
+    if (r < 3 && c < 3) return r == c ? diag(6, r) : -m[6 + 2 + r + c];
+    if (r < 3) {
+        const int b = c - 3;
+        if (r == b) return 0.f;
+        const int l = 3 - r - b;
+        return ((r + 1) % 3 == b) ? m[12 + l] : -m[12 + l];
+    }
+    const int ra = r - 3, cb = c - 3;
+    return ra == cb ? diag(0, ra) : -m[2 + ra + cb];
+}
+
+template <int G>
+__global__ void __launch_bounds__(kGbThreads, 1) gp_build_kernel(BuildArgs a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    GpBuildSmem<G>& S = *reinterpret_cast<GpBuildSmem<G>*>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    const int nbx = (a.nx + 3) / 4, nby = (a.ny + 1) / 2;
+    const int brick = blockIdx.x;
+    const int i0 = 4 * (brick % nbx), j0 = 2 * ((brick / nbx) % nby), k0 = 2 * (brick / (nbx * nby));
+    const int ni = i0 + (warp & 3), nj = j0 + ((warp >> 2) & 1), nk = k0 + (warp >> 3);
+    const bool valid = ni < a.nx && nj < a.ny && nk < a.nz;
+    const float cx = __fadd_rn(a.ox, __fmul_rn(a.res, (float)ni));
+    const float cy = __fadd_rn(a.oy, __fmul_rn(a.res, (float)nj));
+    const float cz = __fadd_rn(a.oz, __fmul_rn(a.res, (float)nk));
+    const float blo[3] = {a.ox + a.res * i0, a.oy + a.res * j0, a.oz + a.res * k0};
+    const float bhi[3] = {a.ox + a.res * min(i0 + 3, a.nx - 1), a.oy + a.res * min(j0 + 1, a.ny - 1),
+                          a.oz + a.res * min(k0 + 1, a.nz - 1)};
+
+    float* hs = &S.hi[0][0][0];
+    float* ls = &S.lo[0][0][0];
+    for (int idx = tid; idx < kGbWarps * kGbMom * G * 32; idx += kGbThreads) {
+        hs[idx] = 0.f;
+        ls[idx] = 0.f;
+    }
+    const int* startp = reinterpret_cast<const int*>(a.ws + a.lay.start);
+    const int nrows = enumerate_runs(a.bg, startp, blo, bhi, a.rcull, S.runs, kGbMaxRuns, tid, kGbThreads, a.err);
+    if (tid == 0) {
+        S.nruns = nrows;
+        for (int s = 0; s < kGbSlots; ++s) mbar_init(&S.bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    const float4* sorted = reinterpret_cast<const float4*>(a.ws + a.lay.sorted);
+    TileProducer<kGbTile> prod;
+    auto produce = [&](int slot) {
+        S.tile_count[slot] = prod.fill(S.tile[slot], S.runs, S.nruns, sorted, &S.bars[slot]);
+        mbar_arrive(&S.bars[slot]);
+    };
+    if (tid == 0) {
+        fence_proxy_async();
+        for (int s = 0; s < kGbSlots; ++s) produce(s);
+    }
+
+    // this lane's sample axes, scaled so that v = 1 / (1 + 2^(shift - z'.u))
+    float zx[G], zy[G], zz[G];
+#pragma unroll
+    for (int k = 0; k < G; ++k) {
+        const int g = lane + 32 * k;
+        float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (g < a.gp_ns) z = a.gp_axes[g];
+        zx[k] = z.x * a.gp_scale;
+        zy[k] = z.y * a.gp_scale;
+        zz[k] = z.z * a.gp_scale;
+    }
+    const float shift = a.gp_shift;
+    float acc[G][kGbMom];
+#pragma unroll
+    for (int k = 0; k < G; ++k)
+#pragma unroll
+        for (int m = 0; m < kGbMom; ++m) acc[k][m] = 0.f;
+    float* hw = hs + warp * kGbMom * G * 32 + lane;
+    float* lw = ls + warp * kGbMom * G * 32 + lane;
+    auto merge = [&]() {
+#pragma unroll
+        for (int k = 0; k < G; ++k)
+#pragma unroll
+            for (int m = 0; m < kGbMom; ++m) {
+                kahan_merge(hw, lw, (k * kGbMom + m) * 32, acc[k][m]);
+                acc[k][m] = 0.f;
+            }
+    };
+
+    const float rmin2 = a.rmin2, rmax2 = a.rmax2;
+    int inblock = 0;
+    unsigned long long in_pairs = 0, cand = 0;
+    bool ok = true;
+    float4* list = S.list[warp];
+    for (int it = 0;; ++it) {
+        const int slot = it % kGbSlots;
+        const uint32_t par = (uint32_t)((it / kGbSlots) & 1);
+        const bool late = !mbar_wait_bounded(&S.bars[slot], par);
+        if (__syncthreads_or(late)) {
+            ok = false;
+            if (tid == 0) set_error(a.err, FIF_ETIMEOUT);
+            break;
+        }
+        const int cnt = S.tile_count[slot];
+        if (cnt == 0) break;
+        const float4* tile = S.tile[slot];
+        if (valid) {
+            cand += cnt;
+            for (int base = 0; base < cnt; base += 32) {
+                bool in = false;
+                float dx = 0.f, dy = 0.f, dz = 0.f, n2 = 1.f;
+                if (base + lane < cnt) {
+                    const float4 P = tile[base + lane];
+                    dx = __fsub_rn(P.x, cx);
+                    dy = __fsub_rn(P.y, cy);
+                    dz = __fsub_rn(P.z, cz);
+                    n2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+                    in = (n2 > rmin2) && (n2 <= rmax2);
+                }
+                const unsigned mask = __ballot_sync(0xffffffffu, in);
+                if (in) {
+                    const float r = rsqrtf(n2);
+                    list[__popc(mask & ((1u << lane) - 1u))] = make_float4(dx * r, dy * r, dz * r, r);
+                }
+                __syncwarp();
+                const int nin = __popc(mask);
+#pragma unroll 1
+                for (int l = 0; l < nin; ++l) {
+                    const float4 L = list[l];
+                    const float x = L.x, y = L.y, z = L.z, in_ = L.w, w2 = L.w * L.w;
+                    const float xx = x * x, yy = y * y, zz2 = z * z, xy = x * y, xz = x * z, yz = y * z;
+                    const float X[kGbMom] = {xx, yy, zz2, xy, xz, yz, xx * w2, yy * w2, zz2 * w2, xy * w2,
+                                             xz * w2, yz * w2, x * in_, y * in_, z * in_};
+#pragma unroll
+                    for (int k = 0; k < G; ++k) {
+                        float arg = shift - fmaf(zx[k], x, fmaf(zy[k], y, zz[k] * z));
+                        arg = fminf(arg, 60.f);
+                        const float v = rcp_approx(1.f + ex2_approx(arg));
+#pragma unroll
+                        for (int m = 0; m < kGbMom; ++m) acc[k][m] = fmaf(v, X[m], acc[k][m]);
+                    }
+                }
+                __syncwarp();
+                in_pairs += nin;
+                inblock += nin;
+                if (inblock >= kGbBlock) {
+                    merge();
+                    inblock = 0;
+                }
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            fence_proxy_async();
+            produce(slot);
+        }
+    }
+    if (valid && inblock > 0) merge();
+    {
+        unsigned long long* stats = reinterpret_cast<unsigned long long*>(a.ws + a.lay.stats);
+        if (valid && lane == 0) {
+            if (in_pairs) atomicAdd(&stats[0], in_pairs);
+            if (cand) atomicAdd(&stats[1], cand);
+        }
+    }
+    if (!valid) return;
+    if (a.accumulate != 0 && in_pairs == 0) return;   // an update leaves unreached nodes untouched
+    const int64_t node = ni + (int64_t)a.nx * (nj + (int64_t)a.ny * nk);
+    float* out = reinterpret_cast<float*>(a.out) + node * a.stride;
+    const int rs = a.gp_rs;
+#pragma unroll
+    for (int k = 0; k < G; ++k) {
+        const int g = lane + 32 * k;
+        if (g >= rs) continue;
+        float mo[kGbMom];
+#pragma unroll
+        for (int m = 0; m < kGbMom; ++m) mo[m] = hw[(k * kGbMom + m) * 32] - lw[(k * kGbMom + m) * 32];
+        const bool live = ok && g < a.gp_ns;
+#pragma unroll
+        for (int e = 0; e < 21; ++e) {
+            float v = live ? gp_entry(e, mo) * a.inv_sigma2 : 0.f;
+            if (a.accumulate != 0) v = fmaf((float)a.accumulate, v, out[e * rs + g]);
+            out[e * rs + g] = v;
+        }
+    }
+    if (a.accumulate == 0)
+        for (int idx = 21 * rs + lane; idx < a.stride; idx += 32) out[idx] = 0.f;
+}
+
+// ------------------------------------------------------------------------------------
+// query
+// ------------------------------------------------------------------------------------
+constexpr int kGqContract = 8;                 // one warp per corner
+constexpr int kGqWeights = 4;
+constexpr int kGqWarps = kGqContract + kGqWeights + 1;
+constexpr int kGqThreads = kGqWarps * 32;
+constexpr int kGqPB = 4;                       // poses per weights block
+constexpr int kEbRow = 169;                    // floats per pose in the corner table (odd)
+constexpr int kGqMaxStages = 4;
+
+struct GqLayout {
+    int ring, atab, eb, kbuf, bars, flag, total, stages;
+};
+
+// shared-memory layout for S floats per node, row stride rs and `stages` ring slots per warp
+__host__ __device__ inline GqLayout gq_layout(int S, int rs, int stages) {
+    GqLayout L;
+    int off = 0;
+    L.stages = stages;
+    L.ring = off;  off += kGqContract * stages * S * 4;
+    L.atab = off;  off += 2 * 32 * rs * 4;
+    L.eb = off;    off += 2 * 32 * kEbRow * 4;
+    off = (off + 15) / 16 * 16;
+    L.kbuf = off;  off += kGqWeights * kGqPB * rs * 8;
+    off = (off + 7) / 8 * 8;
+    L.bars = off;  off += (kGqContract * kGqMaxStages + 8) * 8;
+    L.flag = off;  off += 16;
+    L.total = (off + 127) / 128 * 128;
+    return L;
+}
+
+struct GqBars {
+    uint64_t full[kGqContract][kGqMaxStages];
+    uint64_t aready[2], afree[2], efull[2], eempty[2];
+};
+
+// lattice cell and trilinear weights of a position (the same arithmetic as query.cu)
+FIF_DEV void gq_cell(const QueryArgs& a, const float t[3], uint32_t& st, int i0[3], float w[3]) {
+    const float org[3] = {a.ox, a.oy, a.oz};
+    const int dims[3] = {a.nx, a.ny, a.nz};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float gg = __fdiv_rn(__fsub_rn(t[c], org[c]), a.res);
+        if (!(st & FIF_POSE_NAN)) {
+            if (gg < 0.f || gg > (float)(dims[c] - 1)) st |= FIF_POSE_OUTSIDE;
+        } else {
+            gg = 0.f;
+        }
+        if (a.flags & FIF_Q_NEAREST) {
+            int ii = (int)floorf(__fadd_rn(gg, 0.5f));
+            ii = max(0, min(ii, dims[c] - 1));
+            const int b0 = min(ii, dims[c] - 2);
+            i0[c] = b0;
+            w[c] = (ii > b0) ? 1.f : 0.f;
+        } else {
+            int ii = (int)floorf(gg);
+            ii = max(0, min(ii, dims[c] - 2));
+            i0[c] = ii;
+            w[c] = fminf(fmaxf(gg - (float)ii, 0.f), 1.f);
+        }
+    }
+}
+
+FIF_DEV uint32_t gq_pose(const QueryArgs& a, int64_t p, float t[3], float q[4]) {
+    const float* ps = a.poses + p * 7;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) t[c] = __ldg(ps + c);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) q[c] = __ldg(ps + 3 + c);
+    bool finite = true;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) finite &= isfinite(t[c]);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) finite &= isfinite(q[c]);
+    const float n2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+    finite &= (n2 > 0.f) && isfinite(n2);
+    uint32_t st = 0;
+    if (!finite) st |= FIF_POSE_NAN;
+    if (fabsf(n2 - 1.f) > 1e-3f) st |= FIF_POSE_QUAT;
+    return st;
+}
+
+// position `it` of this CTA's pose stream (its groups of 32, in order) -> pose index, or -1
+FIF_DEV int64_t gq_stream(int64_t it, int64_t m) {
+    const int64_t k = it >> 5;
+    const int64_t p = ((int64_t)blockIdx.x + k * (int64_t)gridDim.x) * 32 + (it & 31);
+    return p < m ? p : -1;
+}
+
+FIF_DEV bool gq_wait(uint64_t* bar, uint32_t parity, volatile int* flag, int* err) {
+    if (mbar_wait_bounded(bar, parity)) return true;
+    set_error(err, FIF_ETIMEOUT);
+    *flag = 1;
+    return false;
+}
+
+// a += W * K in double-float arithmetic: (W.x + W.y) (K.x + K.y) added to (hi, lo) with an
+// exact product of the high parts (fma) and an exact sum (Knuth's two-sum)
+FIF_DEV void df_fma(float2 Wv, float2 Kv, float& hi, float& lo) {
+    const float p = __fmul_rn(Wv.x, Kv.x);
+    float e = fmaf(Wv.x, Kv.x, -p);
+    e = fmaf(Wv.x, Kv.y, e);
+    e = fmaf(Wv.y, Kv.x, e);
+    const float s = __fadd_rn(hi, p);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(err, e));
+}
+
+template <int G>
+__global__ void __launch_bounds__(kGqThreads, 1) gp_query_kernel(QueryArgs a, GqLayout L) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float* ring = reinterpret_cast<float*>(smem_raw + L.ring);
+    float* atab = reinterpret_cast<float*>(smem_raw + L.atab);
+    float* eb = reinterpret_cast<float*>(smem_raw + L.eb);
+    float2* kbuf = reinterpret_cast<float2*>(smem_raw + L.kbuf);
+    GqBars& B = *reinterpret_cast<GqBars*>(smem_raw + L.bars);
+    volatile int* flag = reinterpret_cast<volatile int*>(smem_raw + L.flag);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int NS = L.stages, rs = a.gp_rs, ns = a.gp_ns, S = a.stride;
+    const int64_t m = a.m;
+    const int64_t groups = (m + 31) / 32;
+
+    if (threadIdx.x == 0) {
+        for (int j = 0; j < kGqContract; ++j)
+            for (int s = 0; s < kGqMaxStages; ++s) mbar_init(&B.full[j][s], 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&B.aready[b], kGqWeights);
+            mbar_init(&B.afree[b], kGqContract);
+            mbar_init(&B.efull[b], kGqContract);
+            mbar_init(&B.eempty[b], 1);
+        }
+        *flag = 0;
+        fence_mbar_init();
+    }
+    for (int idx = threadIdx.x; idx < 2 * 32 * rs; idx += kGqThreads) atab[idx] = 0.f;   // pads stay zero
+    __syncthreads();
+
+    if (warp < kGqContract) {
+        // ================================ contract warp ================================
+        const int j = warp;
+        const int bx = j & 1, by = (j >> 1) & 1, bz = (j >> 2) & 1;
+        float* myring = ring + (size_t)j * NS * S;
+        const int64_t nx = a.nx, nxy = (int64_t)a.nx * a.ny;
+        const float* coeffs = reinterpret_cast<const float*>(a.coeffs);
+        auto issue = [&](int64_t it) {   // lane 0 only
+            const int64_t p = gq_stream(it, m);
+            if (p < 0) return;
+            float t[3], q[4];
+            uint32_t st = gq_pose(a, p, t, q);
+            int i0[3];
+            float w[3];
+            gq_cell(a, t, st, i0, w);
+            const int64_t node = (i0[0] + bx) + nx * (i0[1] + by) + nxy * (i0[2] + bz);
+            uint64_t* bar = &B.full[j][it % NS];
+            fence_proxy_async();
+            mbar_arrive_expect_tx(bar, (uint32_t)S * 4u);
+            bulk_g2s(myring + (it % NS) * S, coeffs + node * S, (uint32_t)S * 4u, bar);
+        };
+        if (lane == 0)
+            for (int64_t it = 0; it < NS - 1; ++it) issue(it);
+        int64_t it = 0;
+        for (;; ++it) {
+            const int64_t p = gq_stream(it, m);
+            if (p < 0 || *flag) break;
+            const int64_t k = it >> 5;
+            const int i = (int)(it & 31);
+            const int b = (int)(k & 1);
+            if (i == 0) {
+                if (!gq_wait(&B.aready[b], (uint32_t)((k >> 1) & 1), flag, a.err)) break;
+                if (k >= 2 && !gq_wait(&B.eempty[b], (uint32_t)(((k >> 1) & 1) ^ 1), flag, a.err)) break;
+            }
+            if (lane == 0) issue(it + NS - 1);
+                if (!gq_wait(&B.full[j][it % NS], (uint32_t)((it / NS) & 1), flag, a.err)) break;
+            float t[3], q[4];
+            uint32_t st = gq_pose(a, p, t, q);
+            int i0[3];
+            float w[3];
+            gq_cell(a, t, st, i0, w);
+            const float wj = (bx ? w[0] : 1.f - w[0]) * (by ? w[1] : 1.f - w[1]) * (bz ? w[2] : 1.f - w[2]);
+            if (lane < 21) {
+                const float2* rec = reinterpret_cast<const float2*>(myring + (it % NS) * S + lane * rs);
+                const float2* av = reinterpret_cast<const float2*>(atab + (b * 32 + i) * rs);
+                float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+                const int n2 = rs >> 1;
+                int g2 = 0;
+                for (; g2 + 1 < n2; g2 += 2) {
+                    const float2 r0 = rec[g2], a0 = av[g2], r1 = rec[g2 + 1], a1 = av[g2 + 1];
+                    acc0.x = fmaf(r0.x, a0.x, acc0.x);
+                    acc0.y = fmaf(r0.y, a0.y, acc0.y);
+                    acc1.x = fmaf(r1.x, a1.x, acc1.x);
+                    acc1.y = fmaf(r1.y, a1.y, acc1.y);
+                }
+                if (g2 < n2) {
+                    const float2 r0 = rec[g2], a0 = av[g2];
+                    acc0.x = fmaf(r0.x, a0.x, acc0.x);
+                    acc0.y = fmaf(r0.y, a0.y, acc0.y);
+                }
+                eb[(b * 32 + i) * kEbRow + j * 21 + lane] = wj * ((acc0.x + acc0.y) + (acc1.x + acc1.y));
+            }
+            __syncwarp();
+            if (i == 31 || gq_stream(it + 1, m) < 0) {
+                if (lane == 0) {
+                    mbar_arrive(&B.efull[b]);
+                    mbar_arrive(&B.afree[b]);
+                }
+            }
+        }
+        // after an early exit, wait (bounded) for this warp's copies that may still be in flight
+        // (stream positions it .. it + NS - 1 at most)
+        if (lane == 0 && *flag) {
+            for (int64_t r = it; r < it + NS; ++r)
+                if (gq_stream(r, m) >= 0) mbar_wait_bounded(&B.full[j][r % NS], (uint32_t)((r / NS) & 1), 100000000ull);
+        }
+    } else if (warp < kGqContract + kGqWeights) {
+        // ================================ weights warp ================================
+        const int w = warp - kGqContract;
+        float2* kb = kbuf + (size_t)w * kGqPB * rs;
+        for (int64_t k = 0;; ++k) {
+            const int64_t g = (int64_t)blockIdx.x + k * gridDim.x;
+            if (g >= groups || *flag) break;
+            const int b = (int)(k & 1);
+            if (k >= 2 && !gq_wait(&B.afree[b], (uint32_t)(((k >> 1) & 1) ^ 1), flag, a.err)) break;
+            const int cnt = (m - g * 32 < 32) ? (int)(m - g * 32) : 32;
+            for (int i0 = w * kGqPB; i0 < cnt; i0 += kGqWeights * kGqPB) {
+                // optical axes of the block's poses in double precision (as the oracle does)
+                double zl[3] = {0.0, 0.0, 0.0};
+                int okl = 0;
+                if (lane < kGqPB && i0 + lane < cnt) {
+                    const float* ps = a.poses + (g * 32 + i0 + lane) * 7 + 3;
+                    const double qw = __ldg(ps), qx = __ldg(ps + 1), qy = __ldg(ps + 2), qz = __ldg(ps + 3);
+                    const double nrm = sqrt(qw * qw + qx * qx + qy * qy + qz * qz);
+                    if (nrm > 0.0 && isfinite(nrm)) {
+                        const double W_ = qw / nrm, X_ = qx / nrm, Y_ = qy / nrm, Z_ = qz / nrm;
+                        zl[0] = 2.0 * (X_ * Z_ + W_ * Y_);
+                        zl[1] = 2.0 * (Y_ * Z_ - W_ * X_);
+                        zl[2] = 1.0 - 2.0 * (X_ * X_ + Y_ * Y_);
+                        okl = 1;
+                    }
+                }
+                // broadcast the block's axes to every lane
+                double zb[kGqPB][3];
+                int okb[kGqPB];
+#pragma unroll
+                for (int qq = 0; qq < kGqPB; ++qq) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) zb[qq][c] = __shfl_sync(0xffffffffu, zl[c], qq);
+                    okb[qq] = __shfl_sync(0xffffffffu, okl, qq);
+                }
+                for (int idx = lane; idx < kGqPB * ns; idx += 32) {
+                    const int qq = idx / ns, h = idx - qq * ns;
+                    double zq0 = zb[0][0], zq1 = zb[0][1], zq2 = zb[0][2];
+                    int okq = okb[0];
+#pragma unroll
+                    for (int r = 1; r < kGqPB; ++r)
+                        if (qq == r) { zq0 = zb[r][0]; zq1 = zb[r][1]; zq2 = zb[r][2]; okq = okb[r]; }
+                    const double* ax = a.gp_axes + 4 * h;
+                    const double d0 = zq0 - __ldg(ax), d1 = zq1 - __ldg(ax + 1), d2 = zq2 - __ldg(ax + 2);
+                    const double K = okq ? exp(-(d0 * d0 + d1 * d1 + d2 * d2) * a.gp_inv2l2) : 0.0;
+                    const float hi = (float)K;
+                    kb[qq * rs + h] = make_float2(hi, (float)(K - (double)hi));
+                }
+                __syncwarp();
+                float ahi[kGqPB][G], alo[kGqPB][G];
+#pragma unroll
+                for (int qq = 0; qq < kGqPB; ++qq)
+#pragma unroll
+                    for (int kk = 0; kk < G; ++kk) ahi[qq][kk] = alo[qq][kk] = 0.f;
+#pragma unroll 2
+                for (int h = 0; h < ns; ++h) {
+                    float2 Kq[kGqPB];
+#pragma unroll
+                    for (int qq = 0; qq < kGqPB; ++qq) Kq[qq] = kb[qq * rs + h];
+#pragma unroll
+                    for (int kk = 0; kk < G; ++kk) {
+                        const int gi = lane + 32 * kk;
+                        const float2 Wv = gi < ns ? __ldg(a.gp_wt + (size_t)h * rs + gi) : make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int qq = 0; qq < kGqPB; ++qq) df_fma(Wv, Kq[qq], ahi[qq][kk], alo[qq][kk]);
+                    }
+                }
+#pragma unroll
+                for (int qq = 0; qq < kGqPB; ++qq) {
+                    if (i0 + qq >= cnt) continue;
+                    float* row = atab + (b * 32 + i0 + qq) * rs;
+#pragma unroll
+                    for (int kk = 0; kk < G; ++kk) {
+                        const int gi = lane + 32 * kk;
+                        if (gi < ns) row[gi] = ahi[qq][kk] + alo[qq][kk];
+                    }
+                }
+                __syncwarp();
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&B.aready[b]);
+        }
+    } else {
+        // ================================ metric warp ================================
+        for (int64_t k = 0;; ++k) {
+            const int64_t g = (int64_t)blockIdx.x + k * gridDim.x;
+            if (g >= groups || *flag) break;
+            const int b = (int)(k & 1);
+            if (!gq_wait(&B.efull[b], (uint32_t)((k >> 1) & 1), flag, a.err)) break;
+            const int cnt = (m - g * 32 < 32) ? (int)(m - g * 32) : 32;
+            if (lane < cnt) {
+                const int64_t p = g * 32 + lane;
+                float t[3], q[4];
+                uint32_t st = gq_pose(a, p, t, q);
+                int i0[3];
+                float w[3];
+                gq_cell(a, t, st, i0, w);
+                const bool world = (a.flags & FIF_Q_WORLD) != 0;
+                Blocks T;
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) T.A[r][c] = T.B[r][c] = T.D[r][c] = 0.f;
+                const float* er = eb + (b * 32 + lane) * kEbRow;
+#pragma unroll 1
+                for (int jj = 0; jj < 8; ++jj) {
+                    float Ep[21];
+#pragma unroll
+                    for (int e = 0; e < 21; ++e) Ep[e] = er[jj * 21 + e];
+                    Blocks E;
+                    unpack(Ep, E);
+                    const float cj[3] = {__fadd_rn(a.ox, __fmul_rn(a.res, (float)(i0[0] + (jj & 1)))),
+                                         __fadd_rn(a.oy, __fmul_rn(a.res, (float)(i0[1] + ((jj >> 1) & 1)))),
+                                         __fadd_rn(a.oz, __fmul_rn(a.res, (float)(i0[2] + (jj >> 2))))};
+                    const float d[3] = {world ? cj[0] : cj[0] - t[0], world ? cj[1] : cj[1] - t[1],
+                                        world ? cj[2] : cj[2] - t[2]};
+                    shift_ref(E, d);
+#pragma unroll
+                    for (int r = 0; r < 3; ++r)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            T.A[r][c] += E.A[r][c];
+                            T.B[r][c] += E.B[r][c];
+                            T.D[r][c] += E.D[r][c];
+                        }
+                }
+                if (!world) {
+                    float R[3][3];
+                    quat_to_rot(q[0], q[1], q[2], q[3], R);
+                    rotate_into(T, R);
+                }
+                float fim[21];
+                pack(T, fim);
+                const bool nan = (st & FIF_POSE_NAN) != 0;
+                if (nan) {
+#pragma unroll
+                    for (int e = 0; e < 21; ++e) fim[e] = __int_as_float(0x7fc00000);
+                }
+                if (a.fim) {
+#pragma unroll
+                    for (int e = 0; e < 21; ++e) a.fim[p * 21 + e] = fim[e];
+                }
+                if (a.flags & FIF_Q_METRICS) {
+                    if (a.flags & FIF_Q_TRACE) {
+                        const double tr = nan ? (double)NAN : (double)trace6(fim);
+                        if (a.metrics) a.metrics[p * 3 + 0] = tr;
+                    }
+                    if (a.flags & FIF_Q_LOGDET) {
+                        double lad;
+                        int sg;
+                        logdet_f64(fim, lad, sg);
+                        if (nan) { lad = NAN; sg = 0; }
+                        if (a.metrics) a.metrics[p * 3 + 1] = lad;
+                        if (a.sign) a.sign[p] = (int8_t)sg;
+                        if (sg <= 0 && !nan) st |= FIF_POSE_NOT_PD;
+                    }
+                    if (a.flags & FIF_Q_LMIN) {
+                        double lm = lambda_min_f64(fim);
+                        if (nan) lm = NAN;
+                        if (a.metrics) a.metrics[p * 3 + 2] = lm;
+                        if (!(lm > 0.0) && !nan) st |= FIF_POSE_NOT_PD;
+                    }
+                }
+                if (a.status) a.status[p] = (int32_t)st;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&B.eempty[b]);
+        }
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------
+// launchers
+// ------------------------------------------------------------------------------------
+template <int G>
+static int launch_gp_build_g(const BuildArgs& a, cudaStream_t stream) {
+    const int smem = (int)sizeof(GpBuildSmem<G>);
+    if (cudaFuncSetAttribute(gp_build_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        return FIF_ECUDA;
+    const int64_t bricks = (int64_t)((a.nx + 3) / 4) * ((a.ny + 1) / 2) * ((a.nz + 1) / 2);
+    if (bricks > (int64_t)INT32_MAX) return FIF_ERANGE;
+    gp_build_kernel<G><<<(unsigned)bricks, kGbThreads, smem, stream>>>(a);
+    return cudaPeekAtLastError() == cudaSuccess ? FIF_OK : FIF_ECUDA;
+}
+
+int launch_gp_build(const BuildArgs& a, cudaStream_t stream) {
+    if (a.gp_ns < 1 || a.gp_ns > FIF_GP_MAX_SAMPLES || !a.gp_axes) return FIF_EINVAL;
+    const int rc = launch_binning(a, stream);
+    if (rc != FIF_OK) return rc;
+    const int G = (a.gp_ns + 31) / 32;
+    if (G == 1) return launch_gp_build_g<1>(a, stream);
+    if (G == 2) return launch_gp_build_g<2>(a, stream);
+    return launch_gp_build_g<3>(a, stream);
+}
+
+template <int G>
+static int launch_gp_query_g(const QueryArgs& a, cudaStream_t stream) {
+    int dev = 0, sms = 0, max_smem = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    int stages = kGqMaxStages;
+    GqLayout L = gq_layout(a.stride, a.gp_rs, stages);
+    while (stages > 2 && L.total > max_smem) L = gq_layout(a.stride, a.gp_rs, --stages);
+    if (L.total > max_smem) return FIF_ERANGE;
+    if (cudaFuncSetAttribute(gp_query_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total) != cudaSuccess)
+        return FIF_ECUDA;
+    const int64_t groups = (a.m + 31) / 32;
+    const int64_t grid = std::min<int64_t>(groups, (int64_t)sms);
+    if (grid <= 0) return FIF_OK;
+    gp_query_kernel<G><<<(unsigned)grid, kGqThreads, L.total, stream>>>(a, L);
+    return cudaPeekAtLastError() == cudaSuccess ? FIF_OK : FIF_ECUDA;
+}
+
+int launch_gp_query(const QueryArgs& a, cudaStream_t stream) {
+    if (a.gp_ns < 1 || a.gp_ns > FIF_GP_MAX_SAMPLES || !a.gp_axes || !a.gp_wt) return FIF_EINVAL;
+    const int G = (a.gp_ns + 31) / 32;
+    if (G == 1) return launch_gp_query_g<1>(a, stream);
+    if (G == 2) return launch_gp_query_g<2>(a, stream);
+    return launch_gp_query_g<3>(a, stream);
+}
+
+GpAuxLayout gp_aux_layout(int ns, int rs) {
+    GpAuxLayout L;
+    size_t off = 0;
+    L.axes_f = off; off = align_up(off + 16 * (size_t)ns, 256);
+    L.axes_d = off; off = align_up(off + 32 * (size_t)ns, 256);
+    L.wt = off;     off = align_up(off + 8 * (size_t)ns * rs, 256);
+    L.total = off;
+    return L;
+}
+
+}  // namespace fif

@@ -6,7 +6,10 @@ library is missing, :func:`lib` raises.
 
 The same names as the C ABI: :func:`field_bytes`, :func:`field_init`,
 :func:`build_workspace_bytes`, :func:`build`, :func:`query`, :func:`query_backward`,
-:func:`pointcloud_fim`, :func:`field_save`, :func:`field_load`, :func:`device_error`.
+:func:`pointcloud_fim`, :func:`field_save`, :func:`field_load`, :func:`device_error`, and for
+the GP visibility model :func:`gp_row_stride`, :func:`gp_stride`, :func:`gp_aux_bytes`,
+:func:`gp_upload`, :func:`gp_fit_length_scale`, :func:`gp_field_bytes`, :func:`field_init_gp`
+(:class:`GPModel` holds an uploaded model).
 :class:`Field` bundles a field with its torch-owned storage, and :class:`FifQuery` is the
 autograd function whose backward is the library's hand-written adjoint.
 """
@@ -25,7 +28,8 @@ LIB_PATH = os.path.join(_HERE, "libfif.so")
 # ---- constants (mirror include/fif.h) -------------------------------------------------
 OK, EINVAL, ESIZE, EALIGN, ECUDA, ETIMEOUT, EIO, EFORMAT, ERANGE = 0, -1, -2, -3, -4, -5, -6, -7, -8
 POSE_OUTSIDE, POSE_QUAT, POSE_NOT_PD, POSE_NAN = 1, 2, 4, 8
-STORAGE_F32, STORAGE_BF16, STORAGE_TRACE = 0, 1, 2
+STORAGE_F32, STORAGE_BF16, STORAGE_TRACE, STORAGE_GP = 0, 1, 2, 3
+GP_MAX_SAMPLES = 96
 Q_TRILINEAR, Q_NEAREST, Q_CAMERA, Q_WORLD = 0x0, 0x1, 0x0, 0x2
 Q_TRACE, Q_LOGDET, Q_LMIN, Q_METRICS = 0x10, 0x20, 0x40, 0x70
 STRIDE = {STORAGE_F32: 216, STORAGE_BF16: 224, STORAGE_TRACE: 12}
@@ -53,9 +57,16 @@ class Pinhole(ctypes.Structure):
                 ("width", ctypes.c_int32), ("height", ctypes.c_int32)]
 
 
+class GPC(ctypes.Structure):
+    _fields_ = [("n_samples", ctypes.c_int32), ("reserved", ctypes.c_int32), ("length_scale", ctypes.c_double),
+                ("noise_var", ctypes.c_double), ("k_s", ctypes.c_double),
+                ("axes", (ctypes.c_double * 3) * GP_MAX_SAMPLES), ("d_aux", ctypes.c_void_p)]
+
+
 class FieldC(ctypes.Structure):
     _fields_ = [("grid", Grid), ("params", Params), ("storage", ctypes.c_int32), ("stride", ctypes.c_int32),
-                ("coeffs", ctypes.c_void_p), ("bytes", ctypes.c_size_t), ("k", ctypes.c_double * 3)]
+                ("coeffs", ctypes.c_void_p), ("bytes", ctypes.c_size_t), ("k", ctypes.c_double * 3),
+                ("gp", GPC)]
 
 
 _lib = None
@@ -81,6 +92,15 @@ _SIGS = {
     "fif_field_save": (_I32, [ctypes.POINTER(FieldC), ctypes.c_char_p, _VP, _VP]),
     "fif_field_load": (_I32, [ctypes.POINTER(FieldC), ctypes.c_char_p, _VP, ctypes.c_size_t, _VP, _VP]),
     "fif_device_error": (_I32, [ctypes.POINTER(_I32), _I32, _VP]),
+    "fif_gp_row_stride": (_I32, [_I32]),
+    "fif_gp_stride": (_I32, [_I32]),
+    "fif_gp_aux_bytes": (ctypes.c_size_t, [_I32]),
+    "fif_gp_upload": (_I32, [ctypes.POINTER(GPC), _VP, ctypes.c_size_t, _VP]),
+    "fif_gp_fit_length_scale": (_I32, [ctypes.POINTER(GPC), ctypes.c_double, ctypes.POINTER(ctypes.c_double), _I32,
+                                       ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
+    "fif_gp_field_bytes": (ctypes.c_size_t, [ctypes.POINTER(Grid), _I32]),
+    "fif_field_init_gp": (_I32, [ctypes.POINTER(FieldC), ctypes.POINTER(Grid), ctypes.POINTER(Params),
+                                 ctypes.POINTER(GPC), _VP, ctypes.c_size_t]),
 }
 SYMBOLS = tuple(_SIGS)
 
@@ -155,6 +175,84 @@ def field_init(grid: Grid, params: Params, storage, coeffs: torch.Tensor) -> Fie
     return f
 
 
+def gp_row_stride(n_samples: int) -> int:
+    return int(lib().fif_gp_row_stride(int(n_samples)))
+
+
+def gp_stride(n_samples: int) -> int:
+    return int(lib().fif_gp_stride(int(n_samples)))
+
+
+def gp_aux_bytes(n_samples: int) -> int:
+    return int(lib().fif_gp_aux_bytes(int(n_samples)))
+
+
+def gp_field_bytes(grid: Grid, n_samples: int) -> int:
+    return int(lib().fif_gp_field_bytes(ctypes.byref(grid), int(n_samples)))
+
+
+def _gp_struct(axes, length_scale, noise_var, k_s) -> GPC:
+    g = GPC()
+    ax = [tuple(float(v) for v in row) for row in axes]
+    if not 1 <= len(ax) <= GP_MAX_SAMPLES:
+        raise FifError(EINVAL, "GP sample count")
+    g.n_samples = len(ax)
+    g.length_scale, g.noise_var, g.k_s = float(length_scale), float(noise_var), float(k_s)
+    for i, row in enumerate(ax):
+        for c in range(3):
+            g.axes[i][c] = row[c]
+    return g
+
+
+def gp_fit_length_scale(axes, bearings, half_fov=math.pi / 4, k_s=15.0, noise_var=1e-10, l_lo=0.05,
+                        l_hi=5.0) -> float:
+    """Maximum-marginal-likelihood length scale (fif_gp_fit_length_scale); bearings [m, 3]."""
+    g = _gp_struct(axes, 1.0, noise_var, k_s)
+    flat = [float(v) for row in bearings for v in row[:3]]
+    arr = (ctypes.c_double * len(flat))(*flat)
+    out = ctypes.c_double(0.0)
+    _check(lib().fif_gp_fit_length_scale(ctypes.byref(g), float(half_fov), arr, len(flat) // 3, float(l_lo),
+                                          float(l_hi), ctypes.byref(out)), "fif_gp_fit_length_scale")
+    return float(out.value)
+
+
+def gp_upload(gp: GPC, aux: torch.Tensor, stream=None):
+    _check(lib().fif_gp_upload(ctypes.byref(gp), _ptr(aux), aux.numel() * aux.element_size(), _stream(stream)),
+           "fif_gp_upload")
+
+
+def field_init_gp(grid: Grid, params: Params, gp: GPC, coeffs: torch.Tensor) -> FieldC:
+    f = FieldC()
+    _check(lib().fif_field_init_gp(ctypes.byref(f), ctypes.byref(grid), ctypes.byref(params), ctypes.byref(gp),
+                                   _ptr(coeffs), coeffs.numel() * coeffs.element_size()), "fif_field_init_gp")
+    return f
+
+
+class GPModel:
+    """GP visibility model (Sec. V-B-2) resident on the device: sample optical axes [N_s, 3],
+    SE length scale (fitted by maximum marginal likelihood when None, from `bearings`), noise
+    variance on the diagonal of K^s and sigmoid sharpness k_s."""
+
+    def __init__(self, axes, length_scale=None, noise_var=1e-10, k_s=15.0, half_fov=math.pi / 4, bearings=None,
+                 device="cuda", stream=None):
+        axes = [tuple(float(v) for v in row) for row in axes]
+        if length_scale is None:
+            if bearings is None:
+                raise ValueError("length_scale or bearings is required")
+            length_scale = gp_fit_length_scale(axes, bearings, half_fov, k_s, noise_var)
+        self.c = _gp_struct(axes, length_scale, noise_var, k_s)
+        self.aux = torch.zeros(gp_aux_bytes(len(axes)), dtype=torch.uint8, device=device)
+        gp_upload(self.c, self.aux, stream)
+
+    @property
+    def n_samples(self):
+        return int(self.c.n_samples)
+
+    @property
+    def length_scale(self):
+        return float(self.c.length_scale)
+
+
 def build_workspace_bytes(field: FieldC, n: int) -> int:
     return int(lib().fif_build_workspace_bytes(ctypes.byref(field), int(n)))
 
@@ -227,18 +325,26 @@ def device_error(reset=True, stream=None) -> int:
 class Field:
     """A field with torch-owned device storage."""
 
-    def __init__(self, origin, res, dims, params: Params | None = None, storage=STORAGE_F32, device="cuda"):
+    def __init__(self, origin, res, dims, params: Params | None = None, storage=STORAGE_F32, device="cuda",
+                 gp: GPModel | None = None):
         self.grid = make_grid(origin, res, dims)
         self.params = params if params is not None else make_params()
+        n_nodes = int(dims[0]) * int(dims[1]) * int(dims[2])
+        self.storage = storage
+        self.gp = gp
+        self.dims = tuple(int(d) for d in dims)
+        if storage == STORAGE_GP:
+            if gp is None:
+                raise FifError(EINVAL, "a GP field needs a GPModel")
+            self.coeffs = torch.zeros(n_nodes, gp_stride(gp.n_samples), dtype=torch.float32, device=device)
+            self.c = field_init_gp(self.grid, self.params, gp.c, self.coeffs)
+            return
         nbytes = field_bytes(self.grid, storage)
         if nbytes == 0:
             raise FifError(EINVAL, "fif_field_bytes")
         dt = torch.bfloat16 if storage == STORAGE_BF16 else torch.float32
-        n_nodes = int(dims[0]) * int(dims[1]) * int(dims[2])
-        self.storage = storage
         self.coeffs = torch.zeros(n_nodes, STRIDE[storage], dtype=dt, device=device)
         self.c = field_init(self.grid, self.params, storage, self.coeffs)
-        self.dims = tuple(int(d) for d in dims)
 
     @property
     def n_nodes(self):
@@ -250,7 +356,10 @@ class Field:
         other = object.__new__(Field)
         other.__dict__.update(self.__dict__)
         other.params = params
-        other.c = field_init(self.grid, params, self.storage, self.coeffs)
+        if self.storage == STORAGE_GP:
+            other.c = field_init_gp(self.grid, params, self.gp.c, self.coeffs)
+        else:
+            other.c = field_init(self.grid, params, self.storage, self.coeffs)
         return other
 
     def build(self, landmarks: torch.Tensor, workspace: torch.Tensor | None = None, stream=None):
