@@ -48,6 +48,10 @@ BUILD_FLOPS_PER_PAIR = 151   # shell test 8, rsqrt 1, bearing 4, monomials 31, 6
 # valid while the kernel sources hash to the recorded digest
 QUERY_TRAFFIC = {"bytes_per_pose": (28.977606e9 + 0.475273e9) / 4194304,
                  "digest": "eba6f757ea1849e9"}
+# GP build, per (in-shell pair, sample axis): sigmoid 10 (dot 6, shift 1, exp 1, add 1, rcp 1)
+# + 15 moment accumulations 30; per pair: bearing products 16
+GP_FLOPS_PER_PAIR_SAMPLE = 40
+GP_FLOPS_PER_PAIR = 16
 SMS = 152
 FP32_LANES = 128
 SM_MAX_MHZ = 2070.0
@@ -227,6 +231,44 @@ def run_reference(args):
     return 0
 
 
+def gp_block(fif, synth, spec, lm, r_max, m, ns, dev, stream, hbm_peak, build_steps=2, query_steps=10):
+    """GP-visibility field (Sec. V-B-2): N_s spherical-Fibonacci sample axes, length scale fitted
+    by maximum marginal likelihood on 2000 random bearings, build on the lattice, then m
+    uniform-random poses."""
+    import torch
+    t0 = time.perf_counter()
+    l = fif.gp_fit_length_scale(synth.fibonacci_sphere(ns), synth.sphere_points(7, 2000))
+    fit_s = time.perf_counter() - t0
+    gp = fif.GPModel(synth.fibonacci_sphere(ns), l)
+    fgp = fif.Field(spec.origin, spec.res, spec.dims, fif.make_params(r_max=r_max), storage=fif.STORAGE_GP, gp=gp)
+    ws = torch.empty(fif.build_workspace_bytes(fgp.c, lm.shape[0]), dtype=torch.uint8, device=dev)
+    tb = time_events(lambda: fif.build(fgp.c, lm, ws), build_steps, 1, stream)
+    ins, cnd, _ = fif.build_stats(ws, fgp, lm.shape[0])
+    tb_ms = float(np.mean(tb))
+    flops = ins * (GP_FLOPS_PER_PAIR_SAMPLE * ns + GP_FLOPS_PER_PAIR) / (tb_ms * 1e-3) / 1e12
+    nominal_fp32 = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    poses = torch.from_numpy(synth.random_poses(3000, m, spec.lo, spec.hi)).to(dev)
+    met = torch.empty(m, 3, dtype=torch.float64, device=dev)
+    sg = torch.empty(m, dtype=torch.int8, device=dev)
+    st = torch.empty(m, dtype=torch.int32, device=dev)
+    tq = time_events(lambda: fif.query(fgp.c, poses, fif.Q_METRICS, None, met, sg, st), query_steps, 3, stream)
+    tq_ms = float(np.mean(tq))
+    bpp = 8 * fif.gp_stride(ns) * 4 + 7 * 4 + 3 * 8 + 1 + 4
+    ach = m * bpp / (tq_ms * 1e-3) / 1e9
+    assert fif.device_error() == 0
+    out = {"n_samples": ns, "length_scale": l, "fit_s": fit_s, "field_bytes": fgp.coeffs.numel() * 4,
+           "build_ms": tb_ms, "in_shell_pairs": ins, "build_pairs_per_s": ins / (tb_ms * 1e-3),
+           "build_roofline": {"bound": "alu", "achieved": flops, "peak": nominal_fp32, "unit": "TFLOP/s",
+                              "frac": flops / nominal_fp32,
+                              "flops_per_pair": GP_FLOPS_PER_PAIR_SAMPLE * ns + GP_FLOPS_PER_PAIR},
+           "queries_per_s": m / (tq_ms * 1e-3), "query_kernel_ms": tq_ms, "poses": m, "bytes_per_pose": bpp,
+           "query_roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                              "frac": ach / hbm_peak}}
+    del fgp, ws, poses
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -234,8 +276,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--poses", type=int, default=1 << 22)
-    ap.add_argument("--phase", default="all", choices=["all", "query", "build"],
-                    help="build: time only the build; query: build once untimed, time only the query")
+    ap.add_argument("--phase", default="all", choices=["all", "query", "build", "gp"],
+                    help="build: time only the build; query: build once untimed, time only the query; "
+                         "gp: only the GP-visibility field block")
+    ap.add_argument("--gp-samples", type=int, default=70, help="GP sample axes N_s of the GP block")
     ap.add_argument("--build-nz", type=int, default=40, help="lattice z-layers (smaller for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 2M-landmark building map")
@@ -268,8 +312,15 @@ def main():
     scene = synth.warehouse(seed=2, n=200_000)
     r_max = 10.0
     params = fif.make_params(r_max=r_max, v_alpha=0.5)
-    field = fif.Field(spec.origin, spec.res, spec.dims, params)
     lm = torch.from_numpy(scene.landmarks).to(dev)
+    if args.phase == "gp":
+        gpo = gp_block(fif, synth, spec, lm, r_max, args.poses, args.gp_samples, dev, stream, hbm_peak)
+        if rank == 0:
+            print(json.dumps({"metric": "GP-field queries/s", "value": gpo["queries_per_s"], "unit": "queries/s",
+                              "n_gpus": ws, "config": {"workload": WORKLOAD, "lattice": list(spec.dims)},
+                              "gp": gpo}), flush=True)
+        return 0
+    field = fif.Field(spec.origin, spec.res, spec.dims, params)
     wsb = torch.empty(fif.build_workspace_bytes(field.c, lm.shape[0]), dtype=torch.uint8, device=dev)
 
     out = {}
@@ -394,6 +445,9 @@ def main():
                           "roofline": {"bound": "hbm", "achieved": m * btr / (float(np.mean(ttq)) * 1e-3) / 1e9,
                                        "peak": hbm_peak, "unit": "GB/s"}}
     del ftr
+
+    # ---------------- GP visibility field (N_s = 70, the paper's choice) ----------------
+    out["gp"] = gp_block(fif, synth, spec, lm, r_max, m, args.gp_samples, dev, stream, hbm_peak)
 
     # ---------------- differentiable trajectory batch (256 x 128 samples) ----------------
     from paper_2008_03324_gb300 import traj

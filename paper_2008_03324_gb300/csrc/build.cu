@@ -57,34 +57,6 @@ __device__ __constant__ int8_t kVp[10][3] = {{2, 0, 0}, {0, 2, 0}, {0, 0, 2}, {1
 // moment blocks: base index of (power of 1/n, degree)
 constexpr int kS4n2 = 0, kS3n2 = 15, kS3n1 = 25, kS2n1 = 35, kS4n0 = 41, kS3n0 = 56;
 
-// packed single-precision pairs (sm_100+ f32x2 instructions: one issue slot, two lanes' worth
-// of FP32 work; each half rounds exactly like the scalar instruction)
-__device__ __forceinline__ unsigned long long pk2(float2 v) {
-    unsigned long long u;
-    memcpy(&u, &v, 8);
-    return u;
-}
-__device__ __forceinline__ float2 upk2(unsigned long long u) {
-    float2 v;
-    memcpy(&v, &u, 8);
-    return v;
-}
-__device__ __forceinline__ float2 add2(float2 a, float2 b) {
-    unsigned long long d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
-    return upk2(d);
-}
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
-    unsigned long long d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
-    return upk2(d);
-}
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
-    unsigned long long d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)), "l"(pk2(c)));
-    return upk2(d);
-}
-
 // ------------------------------------------------------------------------------------
 // binning
 // ------------------------------------------------------------------------------------

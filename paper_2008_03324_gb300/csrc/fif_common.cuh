@@ -5,6 +5,8 @@
 // the information metrics (Sec. IV of the paper: trace, determinant, smallest eigenvalue).
 #pragma once
 
+#include <cstring>
+
 #include <cstdint>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -389,6 +391,39 @@ FIF_DEV void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
 // bulk prefetch of global memory into L2 (address and size multiples of 16)
 FIF_DEV void bulk_prefetch_l2(const void* src, uint32_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
+// packed single-precision pairs (sm_100+ f32x2 instructions: one issue slot, two lanes' worth
+// of FP32 work; each half rounds exactly like the scalar instruction)
+FIF_DEV unsigned long long pk2(float2 v) {
+    unsigned long long u;
+    memcpy(&u, &v, 8);
+    return u;
+}
+FIF_DEV float2 upk2(unsigned long long u) {
+    float2 v;
+    memcpy(&v, &u, 8);
+    return v;
+}
+FIF_DEV float2 add2(float2 a, float2 b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
+    return upk2(d);
+}
+FIF_DEV float2 sub2(float2 a, float2 b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
+    return upk2(d);
+}
+FIF_DEV float2 mul2(float2 a, float2 b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
+    return upk2(d);
+}
+FIF_DEV float2 fma2(float2 a, float2 b, float2 c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)), "l"(pk2(c)));
+    return upk2(d);
 }
 
 // record a device-side failure (first code wins)

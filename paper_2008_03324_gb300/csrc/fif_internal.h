@@ -104,7 +104,7 @@ int launch_gp_build(const BuildArgs& a, cudaStream_t stream);
 struct GpAuxLayout {
     size_t axes_f;   // float4[ns]
     size_t axes_d;   // double[ns][4]
-    size_t wt;       // float2[ns][rs]
+    size_t wt;       // float2[ns][rs] (high, low)
     size_t total;
 };
 GpAuxLayout gp_aux_layout(int ns, int rs);

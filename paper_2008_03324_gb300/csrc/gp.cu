@@ -141,33 +141,60 @@ __global__ void __launch_bounds__(kGbThreads, 1) gp_build_kernel(BuildArgs a) {
         for (int s = 0; s < kGbSlots; ++s) produce(s);
     }
 
-    // this lane's sample axes, scaled so that v = 1 / (1 + 2^(shift - z'.u))
-    float zx[G], zy[G], zz[G];
+    // this lane's sample axes, scaled and negated so that v = 1 / (1 + 2^(shift + nz.u))
+    float nzx[G], nzy[G], nzz[G];
 #pragma unroll
     for (int k = 0; k < G; ++k) {
         const int g = lane + 32 * k;
         float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
         if (g < a.gp_ns) z = a.gp_axes[g];
-        zx[k] = z.x * a.gp_scale;
-        zy[k] = z.y * a.gp_scale;
-        zz[k] = z.z * a.gp_scale;
+        nzx[k] = -z.x * a.gp_scale;
+        nzy[k] = -z.y * a.gp_scale;
+        nzz[k] = -z.z * a.gp_scale;
     }
     const float shift = a.gp_shift;
-    float acc[G][kGbMom];
+    // moment sums of the current block, packed in pairs of moments: (xx, yy) (zz, xy) (xz, yz),
+    // the same over n^2, (x, y) / n, and z / n alone
+    float2 acc[G][7];
+    float accz[G];
 #pragma unroll
-    for (int k = 0; k < G; ++k)
+    for (int k = 0; k < G; ++k) {
 #pragma unroll
-        for (int m = 0; m < kGbMom; ++m) acc[k][m] = 0.f;
+        for (int q = 0; q < 7; ++q) acc[k][q] = make_float2(0.f, 0.f);
+        accz[k] = 0.f;
+    }
     float* hw = hs + warp * kGbMom * G * 32 + lane;
     float* lw = ls + warp * kGbMom * G * 32 + lane;
     auto merge = [&]() {
 #pragma unroll
-        for (int k = 0; k < G; ++k)
+        for (int k = 0; k < G; ++k) {
 #pragma unroll
-            for (int m = 0; m < kGbMom; ++m) {
-                kahan_merge(hw, lw, (k * kGbMom + m) * 32, acc[k][m]);
-                acc[k][m] = 0.f;
+            for (int q = 0; q < 7; ++q) {
+                kahan_merge(hw, lw, (k * kGbMom + 2 * q) * 32, acc[k][q].x);
+                kahan_merge(hw, lw, (k * kGbMom + 2 * q + 1) * 32, acc[k][q].y);
+                acc[k][q] = make_float2(0.f, 0.f);
             }
+            kahan_merge(hw, lw, (k * kGbMom + 14) * 32, accz[k]);
+            accz[k] = 0.f;
+        }
+    };
+    // v_g of the bearing (x, y, z) for every owned sample axis, two axes per packed step
+    auto sigmoids = [&](float x, float y, float z, float* v) {
+#pragma unroll
+        for (int k = 0; k + 1 < G; k += 2) {
+            float2 arg = fma2(make_float2(nzx[k], nzx[k + 1]), make_float2(x, x),
+                              fma2(make_float2(nzy[k], nzy[k + 1]), make_float2(y, y),
+                                   fma2(make_float2(nzz[k], nzz[k + 1]), make_float2(z, z), make_float2(shift, shift))));
+            const float2 E = make_float2(ex2_approx(fminf(arg.x, 60.f)), ex2_approx(fminf(arg.y, 60.f)));
+            const float2 d = add2(E, make_float2(1.f, 1.f));
+            v[k] = rcp_approx(d.x);
+            v[k + 1] = rcp_approx(d.y);
+        }
+        if (G & 1) {
+            const int k = G - 1;
+            const float arg = fmaf(nzx[k], x, fmaf(nzy[k], y, fmaf(nzz[k], z, shift)));
+            v[k] = rcp_approx(1.f + ex2_approx(fminf(arg, 60.f)));
+        }
     };
 
     const float rmin2 = a.rmin2, rmax2 = a.rmax2;
@@ -211,16 +238,22 @@ __global__ void __launch_bounds__(kGbThreads, 1) gp_build_kernel(BuildArgs a) {
                 for (int l = 0; l < nin; ++l) {
                     const float4 L = list[l];
                     const float x = L.x, y = L.y, z = L.z, in_ = L.w, w2 = L.w * L.w;
-                    const float xx = x * x, yy = y * y, zz2 = z * z, xy = x * y, xz = x * z, yz = y * z;
-                    const float X[kGbMom] = {xx, yy, zz2, xy, xz, yz, xx * w2, yy * w2, zz2 * w2, xy * w2,
-                                             xz * w2, yz * w2, x * in_, y * in_, z * in_};
+                    const float2 xy = make_float2(x, y);
+                    const float2 m0 = mul2(xy, xy);                               // xx, yy
+                    const float2 m1 = mul2(make_float2(z, x), make_float2(z, y));  // zz, xy
+                    const float2 m2 = mul2(xy, make_float2(z, z));                 // xz, yz
+                    const float2 ww = make_float2(w2, w2);
+                    const float2 X[7] = {m0, m1, m2, mul2(m0, ww), mul2(m1, ww), mul2(m2, ww),
+                                         mul2(xy, make_float2(in_, in_))};
+                    const float zi = z * in_;
+                    float v[G];
+                    sigmoids(x, y, z, v);
 #pragma unroll
                     for (int k = 0; k < G; ++k) {
-                        float arg = shift - fmaf(zx[k], x, fmaf(zy[k], y, zz[k] * z));
-                        arg = fminf(arg, 60.f);
-                        const float v = rcp_approx(1.f + ex2_approx(arg));
+                        const float2 vv = make_float2(v[k], v[k]);
 #pragma unroll
-                        for (int m = 0; m < kGbMom; ++m) acc[k][m] = fmaf(v, X[m], acc[k][m]);
+                        for (int q = 0; q < 7; ++q) acc[k][q] = fma2(vv, X[q], acc[k][q]);
+                        accz[k] = fmaf(v[k], zi, accz[k]);
                     }
                 }
                 __syncwarp();
@@ -282,20 +315,24 @@ constexpr int kEbRow = 169;                    // floats per pose in the corner 
 constexpr int kGqMaxStages = 4;
 
 struct GqLayout {
-    int ring, atab, eb, kbuf, bars, flag, total, stages;
+    int ring, atab, eb, kbuf, ptab, wsm, bars, flag, total, stages;
+    int w_smem;   // 1: W is staged in shared memory at wsm; 0: read from global memory
 };
 
-// shared-memory layout for S floats per node, row stride rs and `stages` ring slots per warp
-__host__ __device__ inline GqLayout gq_layout(int S, int rs, int stages) {
+// shared-memory layout for S floats per node, row stride rs, N_s samples, `stages` ring slots per
+// contract warp, W in shared memory or not
+__host__ __device__ inline GqLayout gq_layout(int S, int rs, int ns, int stages, int w_smem) {
     GqLayout L;
     int off = 0;
     L.stages = stages;
+    L.w_smem = w_smem;
     L.ring = off;  off += kGqContract * stages * S * 4;
     L.atab = off;  off += 2 * 32 * rs * 4;
     L.eb = off;    off += 2 * 32 * kEbRow * 4;
     off = (off + 15) / 16 * 16;
-    L.kbuf = off;  off += kGqWeights * kGqPB * rs * 8;
-    off = (off + 7) / 8 * 8;
+    L.kbuf = off;  off += kGqWeights * (kGqPB / 2) * rs * 16;
+    L.ptab = off;  off += kGqContract * 2 * 32 * 16;
+    L.wsm = off;   off += w_smem ? ns * rs * 8 : 0;
     L.bars = off;  off += (kGqContract * kGqMaxStages + 8) * 8;
     L.flag = off;  off += 16;
     L.total = (off + 127) / 128 * 128;
@@ -367,18 +404,21 @@ FIF_DEV bool gq_wait(uint64_t* bar, uint32_t parity, volatile int* flag, int* er
     return false;
 }
 
-// a += W * K in double-float arithmetic: (W.x + W.y) (K.x + K.y) added to (hi, lo) with an
-// exact product of the high parts (fma) and an exact sum (Knuth's two-sum)
-FIF_DEV void df_fma(float2 Wv, float2 Kv, float& hi, float& lo) {
-    const float p = __fmul_rn(Wv.x, Kv.x);
-    float e = fmaf(Wv.x, Kv.x, -p);
-    e = fmaf(Wv.x, Kv.y, e);
-    e = fmaf(Wv.y, Kv.x, e);
-    const float s = __fadd_rn(hi, p);
-    const float bb = __fsub_rn(s, hi);
-    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+// (hi, lo) += W K for two poses at once, in double-float arithmetic on packed pairs:
+// W = Wh + Wl (the same for both halves), K = Kh + Kl per pose.  The product of the high parts
+// is split exactly with an fma (two-product), its sum into hi exactly with Knuth's two-sum, and
+// the rounding errors plus the cross terms go to lo.  Only -W.hi is used to form -p, so no
+// packed negation is needed.
+FIF_DEV void df_fma2(float2 Wh, float2 Whn, float2 Wl, float2 Kh, float2 Kl, float2& hi, float2& lo) {
+    const float2 pn = mul2(Whn, Kh);            // -p, exact negation of fl(W K)
+    float2 e = fma2(Wh, Kh, pn);                // W K - p, exact
+    e = fma2(Wh, Kl, e);
+    e = fma2(Wl, Kh, e);
+    const float2 s = sub2(hi, pn);              // hi + p
+    const float2 bb = sub2(s, hi);
+    const float2 err = sub2(sub2(hi, sub2(s, bb)), add2(pn, bb));   // (hi - (s - bb)) + (p - bb)
     hi = s;
-    lo = __fadd_rn(lo, __fadd_rn(err, e));
+    lo = add2(lo, add2(err, e));
 }
 
 template <int G>
@@ -387,7 +427,10 @@ __global__ void __launch_bounds__(kGqThreads, 1) gp_query_kernel(QueryArgs a, Gq
     float* ring = reinterpret_cast<float*>(smem_raw + L.ring);
     float* atab = reinterpret_cast<float*>(smem_raw + L.atab);
     float* eb = reinterpret_cast<float*>(smem_raw + L.eb);
-    float2* kbuf = reinterpret_cast<float2*>(smem_raw + L.kbuf);
+    float4* kbuf = reinterpret_cast<float4*>(smem_raw + L.kbuf);
+    int4* ptab = reinterpret_cast<int4*>(smem_raw + L.ptab);
+    float2* wsm = reinterpret_cast<float2*>(smem_raw + L.wsm);
+    const float2* wsrc = L.w_smem ? wsm : a.gp_wt;
     GqBars& B = *reinterpret_cast<GqBars*>(smem_raw + L.bars);
     volatile int* flag = reinterpret_cast<volatile int*>(smem_raw + L.flag);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -408,6 +451,8 @@ __global__ void __launch_bounds__(kGqThreads, 1) gp_query_kernel(QueryArgs a, Gq
         fence_mbar_init();
     }
     for (int idx = threadIdx.x; idx < 2 * 32 * rs; idx += kGqThreads) atab[idx] = 0.f;   // pads stay zero
+    if (L.w_smem)
+        for (int idx = threadIdx.x; idx < ns * rs; idx += kGqThreads) wsm[idx] = __ldg(a.gp_wt + idx);
     __syncthreads();
 
     if (warp < kGqContract) {
@@ -415,22 +460,35 @@ __global__ void __launch_bounds__(kGqThreads, 1) gp_query_kernel(QueryArgs a, Gq
         const int j = warp;
         const int bx = j & 1, by = (j >> 1) & 1, bz = (j >> 2) & 1;
         float* myring = ring + (size_t)j * NS * S;
+        int4* mytab = ptab + j * 64;    // [2][32]: node of corner j (low, high word), w_j
         const int64_t nx = a.nx, nxy = (int64_t)a.nx * a.ny;
         const float* coeffs = reinterpret_cast<const float*>(a.coeffs);
-        auto issue = [&](int64_t it) {   // lane 0 only
-            const int64_t p = gq_stream(it, m);
-            if (p < 0) return;
-            float t[3], q[4];
-            uint32_t st = gq_pose(a, p, t, q);
-            int i0[3];
-            float w[3];
-            gq_cell(a, t, st, i0, w);
-            const int64_t node = (i0[0] + bx) + nx * (i0[1] + by) + nxy * (i0[2] + bz);
+        // corner j's node and trilinear weight for every pose of group k (lane = pose)
+        auto fill_table = [&](int64_t k) {
+            const int64_t p = ((int64_t)blockIdx.x + k * (int64_t)gridDim.x) * 32 + lane;
+            if (p < m) {
+                float t[3], q[4];
+                uint32_t st = gq_pose(a, p, t, q);
+                int i0[3];
+                float w[3];
+                gq_cell(a, t, st, i0, w);
+                const int64_t node = (i0[0] + bx) + nx * (i0[1] + by) + nxy * (i0[2] + bz);
+                const float wj = (bx ? w[0] : 1.f - w[0]) * (by ? w[1] : 1.f - w[1]) * (bz ? w[2] : 1.f - w[2]);
+                mytab[(k & 1) * 32 + lane] =
+                    make_int4((int)(uint32_t)(node & 0xffffffffu), (int)(node >> 32), __float_as_int(wj), 0);
+            }
+            __syncwarp();
+        };
+        auto issue = [&](int64_t it) {   // lane 0 only; the table of it's group is filled
+            if (gq_stream(it, m) < 0) return;
+            const int4 e = mytab[((it >> 5) & 1) * 32 + (it & 31)];
+            const int64_t node = (int64_t)(uint32_t)e.x | ((int64_t)e.y << 32);
             uint64_t* bar = &B.full[j][it % NS];
             fence_proxy_async();
             mbar_arrive_expect_tx(bar, (uint32_t)S * 4u);
             bulk_g2s(myring + (it % NS) * S, coeffs + node * S, (uint32_t)S * 4u, bar);
         };
+        fill_table(0);
         if (lane == 0)
             for (int64_t it = 0; it < NS - 1; ++it) issue(it);
         int64_t it = 0;
@@ -441,17 +499,13 @@ __global__ void __launch_bounds__(kGqThreads, 1) gp_query_kernel(QueryArgs a, Gq
             const int i = (int)(it & 31);
             const int b = (int)(k & 1);
             if (i == 0) {
+                if ((int64_t)blockIdx.x + (k + 1) * (int64_t)gridDim.x < groups) fill_table(k + 1);
                 if (!gq_wait(&B.aready[b], (uint32_t)((k >> 1) & 1), flag, a.err)) break;
                 if (k >= 2 && !gq_wait(&B.eempty[b], (uint32_t)(((k >> 1) & 1) ^ 1), flag, a.err)) break;
             }
             if (lane == 0) issue(it + NS - 1);
-                if (!gq_wait(&B.full[j][it % NS], (uint32_t)((it / NS) & 1), flag, a.err)) break;
-            float t[3], q[4];
-            uint32_t st = gq_pose(a, p, t, q);
-            int i0[3];
-            float w[3];
-            gq_cell(a, t, st, i0, w);
-            const float wj = (bx ? w[0] : 1.f - w[0]) * (by ? w[1] : 1.f - w[1]) * (bz ? w[2] : 1.f - w[2]);
+            if (!gq_wait(&B.full[j][it % NS], (uint32_t)((it / NS) & 1), flag, a.err)) break;
+            const float wj = __int_as_float(mytab[b * 32 + i].z);
             if (lane < 21) {
                 const float2* rec = reinterpret_cast<const float2*>(myring + (it % NS) * S + lane * rs);
                 const float2* av = reinterpret_cast<const float2*>(atab + (b * 32 + i) * rs);
@@ -459,17 +513,10 @@ __global__ void __launch_bounds__(kGqThreads, 1) gp_query_kernel(QueryArgs a, Gq
                 const int n2 = rs >> 1;
                 int g2 = 0;
                 for (; g2 + 1 < n2; g2 += 2) {
-                    const float2 r0 = rec[g2], a0 = av[g2], r1 = rec[g2 + 1], a1 = av[g2 + 1];
-                    acc0.x = fmaf(r0.x, a0.x, acc0.x);
-                    acc0.y = fmaf(r0.y, a0.y, acc0.y);
-                    acc1.x = fmaf(r1.x, a1.x, acc1.x);
-                    acc1.y = fmaf(r1.y, a1.y, acc1.y);
+                    acc0 = fma2(rec[g2], av[g2], acc0);
+                    acc1 = fma2(rec[g2 + 1], av[g2 + 1], acc1);
                 }
-                if (g2 < n2) {
-                    const float2 r0 = rec[g2], a0 = av[g2];
-                    acc0.x = fmaf(r0.x, a0.x, acc0.x);
-                    acc0.y = fmaf(r0.y, a0.y, acc0.y);
-                }
+                if (g2 < n2) acc0 = fma2(rec[g2], av[g2], acc0);
                 eb[(b * 32 + i) * kEbRow + j * 21 + lane] = wj * ((acc0.x + acc0.y) + (acc1.x + acc1.y));
             }
             __syncwarp();
@@ -489,7 +536,8 @@ __global__ void __launch_bounds__(kGqThreads, 1) gp_query_kernel(QueryArgs a, Gq
     } else if (warp < kGqContract + kGqWeights) {
         // ================================ weights warp ================================
         const int w = warp - kGqContract;
-        float2* kb = kbuf + (size_t)w * kGqPB * rs;
+        float4* kb = kbuf + (size_t)w * (kGqPB / 2) * rs;   // [pose pair][h]: (Kh0, Kh1, Kl0, Kl1)
+        float* kbf = reinterpret_cast<float*>(kb);
         for (int64_t k = 0;; ++k) {
             const int64_t g = (int64_t)blockIdx.x + k * gridDim.x;
             if (g >= groups || *flag) break;
@@ -512,7 +560,6 @@ __global__ void __launch_bounds__(kGqThreads, 1) gp_query_kernel(QueryArgs a, Gq
                         okl = 1;
                     }
                 }
-                // broadcast the block's axes to every lane
                 double zb[kGqPB][3];
                 int okb[kGqPB];
 #pragma unroll
@@ -521,6 +568,7 @@ __global__ void __launch_bounds__(kGqThreads, 1) gp_query_kernel(QueryArgs a, Gq
                     for (int c = 0; c < 3; ++c) zb[qq][c] = __shfl_sync(0xffffffffu, zl[c], qq);
                     okb[qq] = __shfl_sync(0xffffffffu, okl, qq);
                 }
+                // K_z[h] in double precision, split into single-precision high and low parts
                 for (int idx = lane; idx < kGqPB * ns; idx += 32) {
                     const int qq = idx / ns, h = idx - qq * ns;
                     double zq0 = zb[0][0], zq1 = zb[0][1], zq2 = zb[0][2];
@@ -532,37 +580,48 @@ __global__ void __launch_bounds__(kGqThreads, 1) gp_query_kernel(QueryArgs a, Gq
                     const double d0 = zq0 - __ldg(ax), d1 = zq1 - __ldg(ax + 1), d2 = zq2 - __ldg(ax + 2);
                     const double K = okq ? exp(-(d0 * d0 + d1 * d1 + d2 * d2) * a.gp_inv2l2) : 0.0;
                     const float hi = (float)K;
-                    kb[qq * rs + h] = make_float2(hi, (float)(K - (double)hi));
+                    float* slot = kbf + 4 * ((qq >> 1) * rs + h) + (qq & 1);
+                    slot[0] = hi;
+                    slot[2] = (float)(K - (double)hi);
                 }
                 __syncwarp();
-                float ahi[kGqPB][G], alo[kGqPB][G];
+                // a = W K for the 4 poses (two packed pairs), lane g = lane + 32 kk
+                float2 ahi[G][kGqPB / 2], alo[G][kGqPB / 2];
 #pragma unroll
-                for (int qq = 0; qq < kGqPB; ++qq)
+                for (int kk = 0; kk < G; ++kk)
 #pragma unroll
-                    for (int kk = 0; kk < G; ++kk) ahi[qq][kk] = alo[qq][kk] = 0.f;
+                    for (int pp = 0; pp < kGqPB / 2; ++pp) ahi[kk][pp] = alo[kk][pp] = make_float2(0.f, 0.f);
+                const float2 neg1 = make_float2(-1.f, -1.f);
 #pragma unroll 2
                 for (int h = 0; h < ns; ++h) {
-                    float2 Kq[kGqPB];
+                    float4 Kq[kGqPB / 2];
 #pragma unroll
-                    for (int qq = 0; qq < kGqPB; ++qq) Kq[qq] = kb[qq * rs + h];
-#pragma unroll
-                    for (int kk = 0; kk < G; ++kk) {
-                        const int gi = lane + 32 * kk;
-                        const float2 Wv = gi < ns ? __ldg(a.gp_wt + (size_t)h * rs + gi) : make_float2(0.f, 0.f);
-#pragma unroll
-                        for (int qq = 0; qq < kGqPB; ++qq) df_fma(Wv, Kq[qq], ahi[qq][kk], alo[qq][kk]);
-                    }
-                }
-#pragma unroll
-                for (int qq = 0; qq < kGqPB; ++qq) {
-                    if (i0 + qq >= cnt) continue;
-                    float* row = atab + (b * 32 + i0 + qq) * rs;
+                    for (int pp = 0; pp < kGqPB / 2; ++pp) Kq[pp] = kb[pp * rs + h];
 #pragma unroll
                     for (int kk = 0; kk < G; ++kk) {
                         const int gi = lane + 32 * kk;
-                        if (gi < ns) row[gi] = ahi[qq][kk] + alo[qq][kk];
+                        const float2 Wq = gi < ns ? wsrc[h * rs + gi] : make_float2(0.f, 0.f);
+                        const float2 Wh = make_float2(Wq.x, Wq.x), Wl = make_float2(Wq.y, Wq.y);
+                        const float2 Whn = mul2(Wh, neg1);
+#pragma unroll
+                        for (int pp = 0; pp < kGqPB / 2; ++pp)
+                            df_fma2(Wh, Whn, Wl, make_float2(Kq[pp].x, Kq[pp].y), make_float2(Kq[pp].z, Kq[pp].w),
+                                    ahi[kk][pp], alo[kk][pp]);
                     }
                 }
+#pragma unroll
+                for (int pp = 0; pp < kGqPB / 2; ++pp)
+#pragma unroll
+                    for (int half = 0; half < 2; ++half) {
+                        const int qq = 2 * pp + half;
+                        if (i0 + qq >= cnt) continue;
+                        float* row = atab + (b * 32 + i0 + qq) * rs;
+#pragma unroll
+                        for (int kk = 0; kk < G; ++kk) {
+                            const int gi = lane + 32 * kk;
+                            if (gi < ns) row[gi] = half ? ahi[kk][pp].y + alo[kk][pp].y : ahi[kk][pp].x + alo[kk][pp].x;
+                        }
+                    }
                 __syncwarp();
             }
             __syncwarp();
@@ -689,10 +748,16 @@ static int launch_gp_query_g(const QueryArgs& a, cudaStream_t stream) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    int stages = kGqMaxStages;
-    GqLayout L = gq_layout(a.stride, a.gp_rs, stages);
-    while (stages > 2 && L.total > max_smem) L = gq_layout(a.stride, a.gp_rs, --stages);
-    if (L.total > max_smem) return FIF_ERANGE;
+    // prefer W in shared memory (its reads sit on the weights warps' critical path), then as
+    // many ring stages as fit (at least 2); without room for W, read it from global memory
+    GqLayout L;
+    bool found = false;
+    for (int w_smem = 1; w_smem >= 0 && !found; --w_smem)
+        for (int stages = kGqMaxStages; stages >= 2 && !found; --stages) {
+            L = gq_layout(a.stride, a.gp_rs, a.gp_ns, stages, w_smem);
+            found = L.total <= max_smem;
+        }
+    if (!found) return FIF_ERANGE;
     if (cudaFuncSetAttribute(gp_query_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total) != cudaSuccess)
         return FIF_ECUDA;
     const int64_t groups = (a.m + 31) / 32;
