@@ -286,9 +286,9 @@ int32_t fif_query(const fif_field* field, const float* d_poses, int64_t m, int32
         a.gp_rs = fif_gp_row_stride(gp.n_samples);
         const fif::GpAuxLayout L = fif::gp_aux_layout(a.gp_ns, a.gp_rs);
         const unsigned char* aux = static_cast<const unsigned char*>(gp.d_aux);
-        a.gp_axes = reinterpret_cast<const double*>(aux + L.axes_d);
+        a.gp_axes = reinterpret_cast<const float4*>(aux + L.axes_df);
         a.gp_wt = reinterpret_cast<const float2*>(aux + L.wt);
-        a.gp_inv2l2 = 1.0 / (2.0 * gp.length_scale * gp.length_scale);
+        a.gp_consts = reinterpret_cast<const float4*>(aux + L.consts);
         return fif::launch_gp_query(a, stream);
     }
     return fif::launch_query(a, stream);

@@ -28,9 +28,9 @@ struct QueryArgs {
     int* err;
     // GP visibility field (storage FIF_STORAGE_GP)
     int gp_ns, gp_rs;
-    const double* gp_axes;     // [ns][4] (x, y, z, 0)
+    const float4* gp_axes;     // [2][ns]: axes as (high, low) single-precision parts (x, y, z, 0)
     const float2* gp_wt;       // [ns][rs]: (high, low) single-precision parts of W[g][h] at h * rs + g
-    double gp_inv2l2;          // 1 / (2 l^2)
+    const float4* gp_consts;   // [9]: exp constants and table (see gp_model.cu)
 };
 int launch_query(const QueryArgs& a, cudaStream_t stream);
 int launch_gp_query(const QueryArgs& a, cudaStream_t stream);
@@ -103,8 +103,10 @@ int launch_gp_build(const BuildArgs& a, cudaStream_t stream);
 // GP model buffer (fif_gp.d_aux): offsets in bytes
 struct GpAuxLayout {
     size_t axes_f;   // float4[ns]
-    size_t axes_d;   // double[ns][4]
+    size_t axes_df;  // float4[2][ns]: high parts, then low parts
     size_t wt;       // float2[ns][rs] (high, low)
+    size_t consts;   // float4[9]: (C1, C2, C3, 32/ln2), (1/l^2 high, low, 0, 0), then 2^(j/32) for
+                     // j = 0..31 as (high, low) pairs, two per float4
     size_t total;
 };
 GpAuxLayout gp_aux_layout(int ns, int rs);

@@ -306,8 +306,8 @@ __global__ void __launch_bounds__(kGbThreads, 1) gp_build_kernel(BuildArgs a) {
 // ------------------------------------------------------------------------------------
 // query
 // ------------------------------------------------------------------------------------
-constexpr int kGqContract = 8;                 // one warp per corner
-constexpr int kGqWeights = 4;
+constexpr int kGqContract = 4;                 // one warp per x-adjacent corner pair
+constexpr int kGqWeights = 8;                  // one block of kGqPB poses per group each
 constexpr int kGqWarps = kGqContract + kGqWeights + 1;
 constexpr int kGqThreads = kGqWarps * 32;
 constexpr int kGqPB = 4;                       // poses per weights block
@@ -315,7 +315,7 @@ constexpr int kEbRow = 169;                    // floats per pose in the corner 
 constexpr int kGqMaxStages = 4;
 
 struct GqLayout {
-    int ring, atab, eb, kbuf, ptab, wsm, bars, flag, total, stages;
+    int ring, atab, eb, kbuf, ptab, wsm, tab, bars, flag, total, stages;
     int w_smem;   // 1: W is staged in shared memory at wsm; 0: read from global memory
 };
 
@@ -326,13 +326,14 @@ __host__ __device__ inline GqLayout gq_layout(int S, int rs, int ns, int stages,
     int off = 0;
     L.stages = stages;
     L.w_smem = w_smem;
-    L.ring = off;  off += kGqContract * stages * S * 4;
+    L.ring = off;  off += kGqContract * stages * 2 * S * 4;
     L.atab = off;  off += 2 * 32 * rs * 4;
     L.eb = off;    off += 2 * 32 * kEbRow * 4;
     off = (off + 15) / 16 * 16;
     L.kbuf = off;  off += kGqWeights * (kGqPB / 2) * rs * 16;
     L.ptab = off;  off += kGqContract * 2 * 32 * 16;
     L.wsm = off;   off += w_smem ? ns * rs * 8 : 0;
+    L.tab = off;   off += 18 * 16;
     L.bars = off;  off += (kGqContract * kGqMaxStages + 8) * 8;
     L.flag = off;  off += 16;
     L.total = (off + 127) / 128 * 128;
@@ -404,6 +405,78 @@ FIF_DEV bool gq_wait(uint64_t* bar, uint32_t parity, volatile int* flag, int* er
     return false;
 }
 
+// error-free transformations (single precision, round to nearest)
+FIF_DEV void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+FIF_DEV void two_prod(float a, float b, float& p, float& e) {
+    p = __fmul_rn(a, b);
+    e = fmaf(a, b, -p);
+}
+
+// exp(xh + xl) for xh + xl in [-87, 0] as a (high, low) pair of floats: Tang's table-driven
+// method (ACM TOMS 15(2), 1989) carried out in double-float arithmetic.  x = N ln2/32 + r with
+// ln2/32 = C1 + C2 + C3 (C1 has 12 significant bits, so N C1 is exact), exp(x) =
+// 2^(N div 32) 2^((N mod 32)/32) (1 + expm1(r)), |r| <= ln2/64, expm1(r) = r + r^2/2 + r^3 q(r)
+// with q the next four Taylor terms.  k = (C1, C2, C3, 32/ln2); tab[j] = 2^(j/32).
+// Relative error below 2e-13 (checked against double-precision exp over [-87, 0]).
+FIF_DEV float2 exp_df(float xh, float xl, float4 k, const float2* tab) {
+    const float N = rintf(__fmul_rn(xh, k.w));
+    const float r1 = fmaf(-N, k.x, xh);
+    float pn, pe;
+    two_prod(N, k.y, pn, pe);
+    float rh0, re;
+    two_sum(r1, -pn, rh0, re);
+    const float rl0 = __fsub_rn(__fadd_rn(__fsub_rn(re, pe), xl), __fmul_rn(N, k.z));
+    float rh, rl;
+    two_sum(rh0, rl0, rh, rl);
+    const float s = rh * fmaf(rh, fmaf(rh, fmaf(rh, 1.f / 720.f, 1.f / 120.f), 1.f / 24.f), 1.f / 6.f);
+    float r2h, r2e;
+    two_prod(rh, rh, r2h, r2e);
+    const float small = rl + 0.5f * (r2e + 2.f * (rh * rl)) + r2h * s;
+    float ph, pe2;
+    two_sum(rh, 0.5f * r2h, ph, pe2);
+    const float pl = pe2 + small;
+    const int Ni = (int)N;
+    const int j = Ni & 31;
+    const int m = (Ni - j) >> 5;
+    const float2 T = tab[j];
+    float q, qe;
+    two_prod(T.x, ph, q, qe);
+    float sh, se;
+    two_sum(T.x, q, sh, se);
+    const float sl = ((se + T.y) + qe) + fmaf(T.x, pl, T.y * ph);
+    const float scale = __int_as_float((m + 127) << 23);   // 2^m, m >= -126 on this range
+    return make_float2(sh * scale, sl * scale);
+}
+
+// K_z[h] = exp(-|z - z_h|^2 / (2 l^2)) = exp((z.z_h - 1) / l^2) for unit z, z_h given as
+// (high, low) float parts; 1/l^2 = cH + cL.  Relative error below 5e-13.
+FIF_DEV float2 kz_df(const float* zH, const float* zL, float4 aH, float4 aL, float cH, float cL, float4 k,
+                     const float2* tab) {
+    float p0, e0, p1, e1, p2, e2;
+    two_prod(zH[0], aH.x, p0, e0);
+    two_prod(zH[1], aH.y, p1, e1);
+    two_prod(zH[2], aH.z, p2, e2);
+    e0 = fmaf(zH[0], aL.x, fmaf(zL[0], aH.x, e0));
+    e1 = fmaf(zH[1], aL.y, fmaf(zL[1], aH.y, e1));
+    e2 = fmaf(zH[2], aL.z, fmaf(zL[2], aH.z, e2));
+    float s1, f1, s2, f2;
+    two_sum(p0, p1, s1, f1);
+    two_sum(s1, p2, s2, f2);
+    const float tl = ((f1 + f2) + (e0 + e1)) + e2;
+    float yh, ye;
+    two_sum(1.f, -s2, yh, ye);
+    const float yl = ye - tl;
+    float xh, xe;
+    two_prod(yh, cH, xh, xe);
+    const float xl = xe + fmaf(yh, cL, yl * cH);
+    if (!(xh <= 87.f)) return make_float2(0.f, 0.f);
+    return exp_df(-xh, -xl, k, tab);
+}
+
 // (hi, lo) += W K for two poses at once, in double-float arithmetic on packed pairs:
 // W = Wh + Wl (the same for both halves), K = Kh + Kl per pose.  The product of the high parts
 // is split exactly with an fma (two-product), its sum into hi exactly with Knuth's two-sum, and
@@ -430,6 +503,7 @@ __global__ void __launch_bounds__(kGqThreads, 1) gp_query_kernel(QueryArgs a, Gq
     float4* kbuf = reinterpret_cast<float4*>(smem_raw + L.kbuf);
     int4* ptab = reinterpret_cast<int4*>(smem_raw + L.ptab);
     float2* wsm = reinterpret_cast<float2*>(smem_raw + L.wsm);
+    float4* ctab = reinterpret_cast<float4*>(smem_raw + L.tab);   // exp constants and table
     const float2* wsrc = L.w_smem ? wsm : a.gp_wt;
     GqBars& B = *reinterpret_cast<GqBars*>(smem_raw + L.bars);
     volatile int* flag = reinterpret_cast<volatile int*>(smem_raw + L.flag);
@@ -453,17 +527,21 @@ __global__ void __launch_bounds__(kGqThreads, 1) gp_query_kernel(QueryArgs a, Gq
     for (int idx = threadIdx.x; idx < 2 * 32 * rs; idx += kGqThreads) atab[idx] = 0.f;   // pads stay zero
     if (L.w_smem)
         for (int idx = threadIdx.x; idx < ns * rs; idx += kGqThreads) wsm[idx] = __ldg(a.gp_wt + idx);
+    for (int idx = threadIdx.x; idx < 18; idx += kGqThreads) ctab[idx] = __ldg(a.gp_consts + idx);
     __syncthreads();
 
     if (warp < kGqContract) {
         // ================================ contract warp ================================
-        const int j = warp;
-        const int bx = j & 1, by = (j >> 1) & 1, bz = (j >> 2) & 1;
-        float* myring = ring + (size_t)j * NS * S;
-        int4* mytab = ptab + j * 64;    // [2][32]: node of corner j (low, high word), w_j
+        // warp jp owns corners j = 2 jp + bx, bx = 0, 1: the two nodes adjacent along x, which
+        // are contiguous in memory and arrive with one bulk copy
+        const int jp = warp;
+        const int by = jp & 1, bz = jp >> 1;
+        const int S2 = 2 * S;
+        float* myring = ring + (size_t)jp * NS * S2;
+        int4* mytab = ptab + jp * 64;    // [2][32]: node of the pair (low, high word), w of bx = 0, 1
         const int64_t nx = a.nx, nxy = (int64_t)a.nx * a.ny;
         const float* coeffs = reinterpret_cast<const float*>(a.coeffs);
-        // corner j's node and trilinear weight for every pose of group k (lane = pose)
+        // the pair's first node and the two trilinear weights for every pose of group k
         auto fill_table = [&](int64_t k) {
             const int64_t p = ((int64_t)blockIdx.x + k * (int64_t)gridDim.x) * 32 + lane;
             if (p < m) {
@@ -472,21 +550,24 @@ __global__ void __launch_bounds__(kGqThreads, 1) gp_query_kernel(QueryArgs a, Gq
                 int i0[3];
                 float w[3];
                 gq_cell(a, t, st, i0, w);
-                const int64_t node = (i0[0] + bx) + nx * (i0[1] + by) + nxy * (i0[2] + bz);
-                const float wj = (bx ? w[0] : 1.f - w[0]) * (by ? w[1] : 1.f - w[1]) * (bz ? w[2] : 1.f - w[2]);
-                mytab[(k & 1) * 32 + lane] =
-                    make_int4((int)(uint32_t)(node & 0xffffffffu), (int)(node >> 32), __float_as_int(wj), 0);
+                const int64_t node = i0[0] + nx * (i0[1] + by) + nxy * (i0[2] + bz);
+                const float wyz = (by ? w[1] : 1.f - w[1]) * (bz ? w[2] : 1.f - w[2]);
+                mytab[(k & 1) * 32 + lane] = make_int4((int)(uint32_t)(node & 0xffffffffu), (int)(node >> 32),
+                                                       __float_as_int((1.f - w[0]) * wyz), __float_as_int(w[0] * wyz));
             }
             __syncwarp();
         };
-        auto issue = [&](int64_t it) {   // lane 0 only; the table of it's group is filled
-            if (gq_stream(it, m) < 0) return;
+        auto node_of = [&](int64_t it) {   // the table of it's group is filled
             const int4 e = mytab[((it >> 5) & 1) * 32 + (it & 31)];
-            const int64_t node = (int64_t)(uint32_t)e.x | ((int64_t)e.y << 32);
-            uint64_t* bar = &B.full[j][it % NS];
+            return (int64_t)(uint32_t)e.x | ((int64_t)e.y << 32);
+        };
+        auto issue = [&](int64_t it) {   // lane 0 only
+            if (gq_stream(it, m) < 0) return;
+            const int64_t node = node_of(it);
+            uint64_t* bar = &B.full[jp][it % NS];
             fence_proxy_async();
-            mbar_arrive_expect_tx(bar, (uint32_t)S * 4u);
-            bulk_g2s(myring + (it % NS) * S, coeffs + node * S, (uint32_t)S * 4u, bar);
+            mbar_arrive_expect_tx(bar, (uint32_t)S2 * 4u);
+            bulk_g2s(myring + (it % NS) * S2, coeffs + node * S, (uint32_t)S2 * 4u, bar);
         };
         fill_table(0);
         if (lane == 0)
@@ -504,20 +585,33 @@ __global__ void __launch_bounds__(kGqThreads, 1) gp_query_kernel(QueryArgs a, Gq
                 if (k >= 2 && !gq_wait(&B.eempty[b], (uint32_t)(((k >> 1) & 1) ^ 1), flag, a.err)) break;
             }
             if (lane == 0) issue(it + NS - 1);
-            if (!gq_wait(&B.full[j][it % NS], (uint32_t)((it / NS) & 1), flag, a.err)) break;
-            const float wj = __int_as_float(mytab[b * 32 + i].z);
+            if (!gq_wait(&B.full[jp][it % NS], (uint32_t)((it / NS) & 1), flag, a.err)) break;
+            const int4 te = mytab[b * 32 + i];
             if (lane < 21) {
-                const float2* rec = reinterpret_cast<const float2*>(myring + (it % NS) * S + lane * rs);
+                // both corners of the pair at once: each weight pair is loaded once, four
+                // independent accumulators keep several shared-memory loads in flight
                 const float2* av = reinterpret_cast<const float2*>(atab + (b * 32 + i) * rs);
-                float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+                const float2* r0 = reinterpret_cast<const float2*>(myring + (it % NS) * S2 + lane * rs);
+                const float2* r1 = reinterpret_cast<const float2*>(myring + (it % NS) * S2 + S + lane * rs);
+                float2 a0 = make_float2(0.f, 0.f), a1 = a0, c0 = a0, c1 = a0;
                 const int n2 = rs >> 1;
                 int g2 = 0;
+#pragma unroll 4
                 for (; g2 + 1 < n2; g2 += 2) {
-                    acc0 = fma2(rec[g2], av[g2], acc0);
-                    acc1 = fma2(rec[g2 + 1], av[g2 + 1], acc1);
+                    const float2 v0 = av[g2], v1 = av[g2 + 1];
+                    a0 = fma2(r0[g2], v0, a0);
+                    a1 = fma2(r0[g2 + 1], v1, a1);
+                    c0 = fma2(r1[g2], v0, c0);
+                    c1 = fma2(r1[g2 + 1], v1, c1);
                 }
-                if (g2 < n2) acc0 = fma2(rec[g2], av[g2], acc0);
-                eb[(b * 32 + i) * kEbRow + j * 21 + lane] = wj * ((acc0.x + acc0.y) + (acc1.x + acc1.y));
+                if (g2 < n2) {
+                    const float2 v0 = av[g2];
+                    a0 = fma2(r0[g2], v0, a0);
+                    c0 = fma2(r1[g2], v0, c0);
+                }
+                float* er = eb + (b * 32 + i) * kEbRow + 2 * jp * 21 + lane;
+                er[0] = __int_as_float(te.z) * ((a0.x + a0.y) + (a1.x + a1.y));
+                er[21] = __int_as_float(te.w) * ((c0.x + c0.y) + (c1.x + c1.y));
             }
             __syncwarp();
             if (i == 31 || gq_stream(it + 1, m) < 0) {
@@ -531,7 +625,7 @@ __global__ void __launch_bounds__(kGqThreads, 1) gp_query_kernel(QueryArgs a, Gq
         // (stream positions it .. it + NS - 1 at most)
         if (lane == 0 && *flag) {
             for (int64_t r = it; r < it + NS; ++r)
-                if (gq_stream(r, m) >= 0) mbar_wait_bounded(&B.full[j][r % NS], (uint32_t)((r / NS) & 1), 100000000ull);
+                if (gq_stream(r, m) >= 0) mbar_wait_bounded(&B.full[jp][r % NS], (uint32_t)((r / NS) & 1), 100000000ull);
         }
     } else if (warp < kGqContract + kGqWeights) {
         // ================================ weights warp ================================
@@ -545,8 +639,9 @@ __global__ void __launch_bounds__(kGqThreads, 1) gp_query_kernel(QueryArgs a, Gq
             if (k >= 2 && !gq_wait(&B.afree[b], (uint32_t)(((k >> 1) & 1) ^ 1), flag, a.err)) break;
             const int cnt = (m - g * 32 < 32) ? (int)(m - g * 32) : 32;
             for (int i0 = w * kGqPB; i0 < cnt; i0 += kGqWeights * kGqPB) {
-                // optical axes of the block's poses in double precision (as the oracle does)
-                double zl[3] = {0.0, 0.0, 0.0};
+                // optical axes of the block's poses: normalised in double precision (as the
+                // oracle does), then kept as (high, low) float pairs
+                float zl[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                 int okl = 0;
                 if (lane < kGqPB && i0 + lane < cnt) {
                     const float* ps = a.poses + (g * 32 + i0 + lane) * 7 + 3;
@@ -554,35 +649,47 @@ __global__ void __launch_bounds__(kGqThreads, 1) gp_query_kernel(QueryArgs a, Gq
                     const double nrm = sqrt(qw * qw + qx * qx + qy * qy + qz * qz);
                     if (nrm > 0.0 && isfinite(nrm)) {
                         const double W_ = qw / nrm, X_ = qx / nrm, Y_ = qy / nrm, Z_ = qz / nrm;
-                        zl[0] = 2.0 * (X_ * Z_ + W_ * Y_);
-                        zl[1] = 2.0 * (Y_ * Z_ - W_ * X_);
-                        zl[2] = 1.0 - 2.0 * (X_ * X_ + Y_ * Y_);
+                        const double zd[3] = {2.0 * (X_ * Z_ + W_ * Y_), 2.0 * (Y_ * Z_ - W_ * X_),
+                                              1.0 - 2.0 * (X_ * X_ + Y_ * Y_)};
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            zl[c] = (float)zd[c];
+                            zl[3 + c] = (float)(zd[c] - (double)zl[c]);
+                        }
                         okl = 1;
                     }
                 }
-                double zb[kGqPB][3];
+                float zb[kGqPB][6];
                 int okb[kGqPB];
 #pragma unroll
                 for (int qq = 0; qq < kGqPB; ++qq) {
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) zb[qq][c] = __shfl_sync(0xffffffffu, zl[c], qq);
+                    for (int c = 0; c < 6; ++c) zb[qq][c] = __shfl_sync(0xffffffffu, zl[c], qq);
                     okb[qq] = __shfl_sync(0xffffffffu, okl, qq);
                 }
-                // K_z[h] in double precision, split into single-precision high and low parts
+                // K_z[h] as (high, low) float pairs, double-float arithmetic throughout
+                const float4 kc = ctab[0];
+                const float cH = ctab[1].x, cL = ctab[1].y;
+                const float2* etab = reinterpret_cast<const float2*>(ctab + 2);
                 for (int idx = lane; idx < kGqPB * ns; idx += 32) {
                     const int qq = idx / ns, h = idx - qq * ns;
-                    double zq0 = zb[0][0], zq1 = zb[0][1], zq2 = zb[0][2];
+                    float zq[6];
                     int okq = okb[0];
 #pragma unroll
+                    for (int c = 0; c < 6; ++c) zq[c] = zb[0][c];
+#pragma unroll
                     for (int r = 1; r < kGqPB; ++r)
-                        if (qq == r) { zq0 = zb[r][0]; zq1 = zb[r][1]; zq2 = zb[r][2]; okq = okb[r]; }
-                    const double* ax = a.gp_axes + 4 * h;
-                    const double d0 = zq0 - __ldg(ax), d1 = zq1 - __ldg(ax + 1), d2 = zq2 - __ldg(ax + 2);
-                    const double K = okq ? exp(-(d0 * d0 + d1 * d1 + d2 * d2) * a.gp_inv2l2) : 0.0;
-                    const float hi = (float)K;
+                        if (qq == r) {
+#pragma unroll
+                            for (int c = 0; c < 6; ++c) zq[c] = zb[r][c];
+                            okq = okb[r];
+                        }
+                    const float2 K = okq ? kz_df(zq, zq + 3, __ldg(a.gp_axes + h), __ldg(a.gp_axes + ns + h), cH, cL,
+                                                 kc, etab)
+                                         : make_float2(0.f, 0.f);
                     float* slot = kbf + 4 * ((qq >> 1) * rs + h) + (qq & 1);
-                    slot[0] = hi;
-                    slot[2] = (float)(K - (double)hi);
+                    slot[0] = K.x;
+                    slot[2] = K.y;
                 }
                 __syncwarp();
                 // a = W K for the 4 poses (two packed pairs), lane g = lane + 32 kk
@@ -768,7 +875,7 @@ static int launch_gp_query_g(const QueryArgs& a, cudaStream_t stream) {
 }
 
 int launch_gp_query(const QueryArgs& a, cudaStream_t stream) {
-    if (a.gp_ns < 1 || a.gp_ns > FIF_GP_MAX_SAMPLES || !a.gp_axes || !a.gp_wt) return FIF_EINVAL;
+    if (a.gp_ns < 1 || a.gp_ns > FIF_GP_MAX_SAMPLES || !a.gp_axes || !a.gp_wt || !a.gp_consts) return FIF_EINVAL;
     const int G = (a.gp_ns + 31) / 32;
     if (G == 1) return launch_gp_query_g<1>(a, stream);
     if (G == 2) return launch_gp_query_g<2>(a, stream);
@@ -778,9 +885,10 @@ int launch_gp_query(const QueryArgs& a, cudaStream_t stream) {
 GpAuxLayout gp_aux_layout(int ns, int rs) {
     GpAuxLayout L;
     size_t off = 0;
-    L.axes_f = off; off = align_up(off + 16 * (size_t)ns, 256);
-    L.axes_d = off; off = align_up(off + 32 * (size_t)ns, 256);
-    L.wt = off;     off = align_up(off + 8 * (size_t)ns * rs, 256);
+    L.axes_f = off;  off = align_up(off + 16 * (size_t)ns, 256);
+    L.axes_df = off; off = align_up(off + 32 * (size_t)ns, 256);
+    L.wt = off;      off = align_up(off + 8 * (size_t)ns * rs, 256);
+    L.consts = off;  off = align_up(off + 16 * 18, 256);
     L.total = off;
     return L;
 }

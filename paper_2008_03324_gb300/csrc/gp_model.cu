@@ -141,12 +141,34 @@ int32_t fif_gp_upload(fif_gp* gp, void* d_aux, size_t bytes, fif_stream_t stream
     inverse_from_cholesky(K, ns, W);
     std::vector<unsigned char> img(L.total, 0);
     float* af = reinterpret_cast<float*>(img.data() + L.axes_f);
-    double* ad = reinterpret_cast<double*>(img.data() + L.axes_d);
+    float* adf = reinterpret_cast<float*>(img.data() + L.axes_df);
     float* wt = reinterpret_cast<float*>(img.data() + L.wt);
+    float* cst = reinterpret_cast<float*>(img.data() + L.consts);
     for (int g = 0; g < ns; ++g) {
         for (int c = 0; c < 3; ++c) {
-            af[4 * g + c] = (float)axes[g][c];
-            ad[4 * g + c] = axes[g][c];
+            const float hi = (float)axes[g][c];
+            af[4 * g + c] = hi;
+            adf[4 * g + c] = hi;
+            adf[4 * (ns + g) + c] = (float)(axes[g][c] - (double)hi);
+        }
+    }
+    // constants of the double-float exponential (Tang's table-driven method): ln2/32 split as
+    // C1 + C2 + C3 with C1 carrying 12 significant bits (so N * C1 is exact for |N| < 2^12),
+    // 32/ln2 to pick N, 1/l^2 as a (high, low) pair, and the table 2^(j/32) as (high, low) pairs
+    {
+        const double ln2_32 = std::log(2.0) / 32.0;
+        const double c1 = std::ldexp(std::nearbyint(std::ldexp(ln2_32, 17)), -17);
+        const double rest = ln2_32 - c1;
+        const float C1 = (float)c1, C2 = (float)rest, C3 = (float)(rest - (double)C2);
+        const double inv_l2 = 1.0 / (gp->length_scale * gp->length_scale);
+        const float cH = (float)inv_l2, cL = (float)(inv_l2 - (double)cH);
+        const float v[8] = {C1, C2, C3, (float)(32.0 / std::log(2.0)), cH, cL, 0.f, 0.f};
+        std::memcpy(cst, v, sizeof(v));
+        for (int j = 0; j < 32; ++j) {
+            const double t = std::exp2(j / 32.0);
+            const float th = (float)t;
+            cst[8 + 2 * j] = th;
+            cst[8 + 2 * j + 1] = (float)(t - (double)th);
         }
     }
     for (int h = 0; h < ns; ++h)
