@@ -44,10 +44,14 @@ WORKLOAD = ("warehouse 50x50x10 m, 200k landmarks (60% box faces / 40% walls, 40
 QUERY_BYTES_PER_POSE = 8 * 210 * 4 + 7 * 4 + 21 * 4 + 3 * 8 + 1 + 4   # corners + pose + outputs
 BUILD_FLOPS_PER_PAIR = 151   # shell test 8, rsqrt 1, bearing 4, monomials 31, 66 accumulations 107
 # DRAM traffic of one query launch per pose, from the ncu capture summarised in
-# profiles/query_kernel_warehouse_4M.md (read 28.978 GB + write 0.475 GB for 4,194,304 poses),
+# profiles/query_kernel_warehouse_4M.md (read 28.973 GB + write 0.475 GB for 4,194,304 poses),
 # valid while the kernel sources hash to the recorded digest
-QUERY_TRAFFIC = {"bytes_per_pose": (28.977606e9 + 0.475273e9) / 4194304,
-                 "digest": "eba6f757ea1849e9"}
+QUERY_TRAFFIC = {"bytes_per_pose": (28.973279e9 + 0.474722e9) / 4194304,
+                 "digest": "829209c9cbefa037"}
+# the same for the GP query (N_s = 70) from profiles/gp_query_kernel_warehouse_nz8.md
+# (read 11.724 GB + write 0.0115 GB for 262,144 poses on the 200 x 200 x 8 lattice)
+GP_QUERY_TRAFFIC = {"bytes_per_pose": (11.724005e9 + 0.011493e9) / 262144, "n_samples": 70,
+                    "digest": "c8d628ace602e5be"}
 # GP build, per (in-shell pair, sample axis): sigmoid 10 (dot 6, shift 1, exp 1, add 1, rcp 1)
 # + 15 moment accumulations 30; per pair: bearing products 16
 GP_FLOPS_PER_PAIR_SAMPLE = 40
@@ -57,10 +61,10 @@ FP32_LANES = 128
 SM_MAX_MHZ = 2070.0
 
 
-def query_source_digest():
+def query_source_digest(files=("query.cu", "gather.cuh", "fif_common.cuh")):
     import hashlib
     h = hashlib.sha256()
-    for f in ("query.cu", "gather.cuh", "fif_common.cuh"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_2008_03324_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -263,7 +267,10 @@ def gp_block(fif, synth, spec, lm, r_max, m, ns, dev, stream, hbm_peak, build_st
                               "flops_per_pair": GP_FLOPS_PER_PAIR_SAMPLE * ns + GP_FLOPS_PER_PAIR},
            "queries_per_s": m / (tq_ms * 1e-3), "query_kernel_ms": tq_ms, "poses": m, "bytes_per_pose": bpp,
            "query_roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                              "frac": ach / hbm_peak}}
+                              "frac": ach / hbm_peak,
+                              "traffic": (GP_QUERY_TRAFFIC["bytes_per_pose"] * m
+                                          if ns == GP_QUERY_TRAFFIC["n_samples"] and GP_QUERY_TRAFFIC["digest"] ==
+                                          query_source_digest(("gp.cu", "fif_common.cuh")) else None)}}
     del fgp, ws, poses
     torch.cuda.empty_cache()
     return out
