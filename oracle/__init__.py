@@ -376,6 +376,9 @@ def _gp_sigs():
         "or_query_gp_batch": (None, [_D, _D, _D, ctypes.c_int64, ctypes.POINTER(_GPStruct), ctypes.c_int, _D]),
         "or_pc_fim_gp": (None, [_F, ctypes.c_int64, _D, ctypes.c_int64, ctypes.POINTER(Params),
                                 ctypes.POINTER(_GPStruct), ctypes.c_int, _D]),
+        "or_info_threshold": (None, [_F, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(Params), ctypes.c_int,
+                                     ctypes.POINTER(_GPStruct), ctypes.c_int, _D, _D]),
+        "or_info_cost": (None, [_D, ctypes.c_int64, ctypes.c_double, ctypes.c_double, _D, _D]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -485,3 +488,32 @@ def query_gp_from_landmarks(landmarks, grid: Grid, params: Params, gp: GP, poses
     corners = blocks[inv].reshape(nodes.shape[0], 8, gp.ns, 6, 6)
     I = query_gp(corners, w, poses, gp, frame)
     return I, st, nodes, w
+
+
+# ---------------------------------------------------------------------------
+# information threshold and potential cost (Sec. VI-B)
+# ---------------------------------------------------------------------------
+
+MODEL_POINTCLOUD, MODEL_QUAD, MODEL_GP = 0, 1, 2
+
+
+def info_threshold(sets, params: Params, model=MODEL_POINTCLOUD, gp: GP | None = None, exclude_degenerate=True):
+    """sets [n, M, 3] camera-frame landmarks -> (metrics [n, 4] = trace, log|det|, sign,
+    lambda_min; thresholds [3] = mean trace, log|det|, lambda_min)."""
+    S = _f32(sets)
+    n, M = S.shape[0], S.shape[1]
+    met = np.zeros((n, 4))
+    thr = np.zeros(3)
+    gps = ctypes.byref(gp.s) if gp is not None else None
+    _gp_sigs().or_info_threshold(_p(S, ctypes.c_float), n, M, ctypes.byref(params), int(model), gps,
+                                 int(bool(exclude_degenerate)), _p(met, ctypes.c_double), _p(thr, ctypes.c_double))
+    return met, thr
+
+
+def info_cost(v, eps, kq):
+    """Eq. info_pot_cost: (c, dc/dv) for metric values v."""
+    x = _f64(v).reshape(-1)
+    c, dc = np.zeros_like(x), np.zeros_like(x)
+    _gp_sigs().or_info_cost(_p(x, ctypes.c_double), x.shape[0], float(eps), float(kq), _p(c, ctypes.c_double),
+                            _p(dc, ctypes.c_double))
+    return c, dc

@@ -1022,3 +1022,71 @@ void or_pc_fim_gp(const float* lm, int64_t n, const double* poses, int64_t m, co
         }
     }
 }
+
+/* ------------------------------------------------------------------------- */
+/* Information threshold and potential cost (Sec. VI-B, Eq. info_pot_cost)     */
+/* ------------------------------------------------------------------------- */
+
+/* Information threshold (Sec. VI-B): n sets of M landmarks in the camera frame (camera at the
+ * origin, optical axis +z), each satisfying the specification (in the FoV, d_min..d_max).  The
+ * FIM a map representation gives for a set, at the camera:
+ *   model 0, point cloud: every landmark counts (v = 1; all are in the FoV by construction);
+ *   model 1, quadratic field: v = v_quad(cos theta) (Eq. quad_vis_approx) -- what a field built
+ *            from the set returns when queried at the node the camera sits on (Eq. fim_separation);
+ *   model 2, GP field: v = v_gp(e3; u) (Eq. gp_vis_approx), likewise;
+ * I_s = sum_i v_i I_i with I_i the camera-frame information of one bearing (Eq. fim_gaussian,
+ * local perturbation).  metrics[s] = (trace, log|det|, sign, lambda_min); the threshold of a
+ * metric is its mean over the sets, over the well-conditioned ones only when
+ * exclude_degenerate (the paper's remedy for degenerate configurations: det > 0 and
+ * lambda_min > 1e-6 trace, a condition-number test above single-precision noise); NaN when
+ * none count. */
+void or_info_threshold(const float* sets, int64_t n, int M, const or_params* prm, int model, const or_gp* gp,
+                       int exclude_degenerate, double* metrics /*[n][4]*/, double* thr /*[3]*/) {
+    double kq[3];
+    or_quad_coeffs(prm->half_fov, prm->v_alpha, kq);
+    const double Rid[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}, t0[3] = {0, 0, 0}, e3[3] = {0, 0, 1};
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t s = 0; s < n; ++s) {
+        double I[36];
+        memset(I, 0, sizeof(I));
+        for (int i = 0; i < M; ++i) {
+            const float* pf = sets + 3 * ((size_t)s * M + i);
+            double p[3] = {pf[0], pf[1], pf[2]};
+            double nn = sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+            double u[3] = {p[0] / nn, p[1] / nn, p[2] / nn};
+            double v = 1.0;
+            if (model == 1) v = kq[2] * u[2] * u[2] + kq[1] * u[2] + kq[0];
+            else if (model == 2) v = or_gp_visibility(gp->axes, gp->ns, gp->W, gp->l, gp->ks, gp->cos_alpha, e3, u);
+            double J[18], Ii[36];
+            or_jac_local(p, Rid, t0, J);
+            or_fim_gauss(J, prm->sigma, Ii);
+            for (int e = 0; e < 36; ++e) I[e] += v * Ii[e];
+        }
+        or_metrics(I, 1, metrics + 4 * s);
+    }
+    double sum[3] = {0, 0, 0};
+    int64_t cnt = 0;
+    for (int64_t s = 0; s < n; ++s) {
+        const double* m4 = metrics + 4 * s;
+        if (exclude_degenerate && !(m4[2] > 0.0 && m4[3] > 1e-6 * m4[0])) continue;
+        sum[0] += m4[0]; sum[1] += m4[1]; sum[2] += m4[3];
+        ++cnt;
+    }
+    for (int c = 0; c < 3; ++c) thr[c] = cnt ? sum[c] / (double)cnt : NAN;
+}
+
+/* Information potential cost (Eq. info_pot_cost) of metric values v with threshold eps > 0 and
+ * k_q > 0:  c = 0 for v > eps;  k_q (v - eps)^2 for 0 <= v <= eps;  k_l v + b_l for v < 0, with
+ * k_l, b_l making c and dc/dv continuous at v = 0: k_l = -2 k_q eps, b_l = k_q eps^2.  Readings:
+ * the printed middle case's (v - c) is taken as (v - eps), and the continuity "at c = 0" as at
+ * v = 0.  Also returns dc/dv.  NaN in, NaN out. */
+void or_info_cost(const double* v, int64_t m, double eps, double kq, double* c, double* dc) {
+    const double kl = -2.0 * kq * eps, bl = kq * eps * eps;
+    for (int64_t i = 0; i < m; ++i) {
+        const double x = v[i];
+        if (x != x) { c[i] = x; dc[i] = x; }
+        else if (x > eps) { c[i] = 0.0; dc[i] = 0.0; }
+        else if (x >= 0.0) { c[i] = kq * (x - eps) * (x - eps); dc[i] = 2.0 * kq * (x - eps); }
+        else { c[i] = kl * x + bl; dc[i] = kl; }
+    }
+}

@@ -425,3 +425,17 @@ class GridSpec:
 ROOM_GRID = GridSpec((0.0, 0.0, 0.0), 0.5, (21, 21, 7))
 WAREHOUSE_GRID = GridSpec((0.125, 0.125, 0.125), 0.25, (200, 200, 40))
 BUILDING_GRID = GridSpec((0.125, 0.125, 0.125), 0.25, (400, 400, 80))
+
+
+def threshold_sets(seed: int, n: int, m: int, d_min: float = 0.3, d_max: float = 1.0,
+                   half_fov: float = math.pi / 4) -> np.ndarray:
+    """n sets of m landmarks meeting the localisation specification of the information
+    threshold: inside the camera's field of view (a cone of half-angle half_fov about +z) at a
+    distance in [d_min, d_max], uniform over that volume (cos theta and r^3 uniform).
+    Camera frame, float32 [n, m, 3]."""
+    rng = _rng(seed)
+    ct = rng.uniform(math.cos(half_fov), 1.0, size=(n, m))
+    st = np.sqrt(np.maximum(0.0, 1.0 - ct * ct))
+    ph = rng.uniform(0.0, 2.0 * math.pi, size=(n, m))
+    r = np.cbrt(rng.uniform(d_min ** 3, d_max ** 3, size=(n, m)))
+    return np.stack([r * st * np.cos(ph), r * st * np.sin(ph), r * ct], axis=-1).astype(np.float32)
