@@ -456,6 +456,28 @@ def main():
     # ---------------- GP visibility field (N_s = 70, the paper's choice) ----------------
     out["gp"] = gp_block(fif, synth, spec, lm, r_max, m, args.gp_samples, dev, stream, hbm_peak)
 
+    # ---------------- information threshold and potential cost (Sec. VI-B) ----------------
+    # 10,000 sets of 200 landmarks at 0.3-1.0 m in the field of view (the paper's specification)
+    sets = torch.from_numpy(synth.threshold_sets(21, 10_000, 200, 0.3, 1.0)).to(dev)
+    thr_out = {}
+    gpc = fif.gp_struct(synth.fibonacci_sphere(args.gp_samples), out["gp"]["length_scale"])
+    for name, model in (("pointcloud", fif.MODEL_POINTCLOUD), ("quad", fif.MODEL_QUAD), ("gp", fif.MODEL_GP)):
+        tmet = torch.empty(10_000, 3, dtype=torch.float64, device=dev)
+        tthr = torch.empty(3, dtype=torch.float64, device=dev)
+        tt = time_events(lambda: fif.info_threshold(params, sets, model, gpc if model == fif.MODEL_GP else None,
+                                                    metrics=tmet, threshold=tthr), 5, 2, stream)
+        thr_out[name] = {"ms": float(np.mean(tt)), "thresholds": [float(x) for x in tthr.cpu()]}
+    cst = torch.empty(m, dtype=torch.float64, device=dev)
+    dcst = torch.empty(m, dtype=torch.float64, device=dev)
+    eps_ld = thr_out["quad"]["thresholds"][1]
+    tc = time_events(lambda: fif.info_cost(met, eps_ld, 0.05, column=1, cost=cst, dcost=dcst), 10, 3, stream)
+    tc_ms = float(np.mean(tc))
+    out["info"] = {"sets": 10_000, "landmarks_per_set": 200, "threshold": thr_out,
+                   "cost_ms": tc_ms, "cost_values_per_s": m / (tc_ms * 1e-3),
+                   "cost_roofline": {"bound": "hbm", "achieved": m * 24 / (tc_ms * 1e-3) / 1e9, "peak": hbm_peak,
+                                     "unit": "GB/s", "frac": m * 24 / (tc_ms * 1e-3) / 1e9 / hbm_peak}}
+    del sets
+
     # ---------------- differentiable trajectory batch (256 x 128 samples) ----------------
     from paper_2008_03324_gb300 import traj
     ctrl_np, yaw_np, basis_np = synth.bspline_batch(6, scene, 256, 32, 128)

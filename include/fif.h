@@ -317,6 +317,39 @@ FIF_API int32_t fif_pointcloud_fim(const float* d_landmarks, int64_t n, const fi
                            int32_t flags, float* d_fim, double* d_metrics, int8_t* d_sign,
                            int32_t* d_status, fif_stream_t stream);
 
+/* ---- information threshold and potential cost (Sec. VI-B) ------------------------------ */
+#define FIF_MODEL_POINTCLOUD 0   /* the point cloud: every landmark of a set counts (v = 1)     */
+#define FIF_MODEL_QUAD 1         /* a quadratic-visibility field (v = v_quad(cos theta))        */
+#define FIF_MODEL_GP 2           /* a GP-visibility field (v = v_gp(e3; u))                     */
+
+/* Information threshold (Sec. VI-B): the metric a map representation gives, averaged over
+ * sets of landmarks that meet a localisation specification (M landmarks in the field of view
+ * at distances d_min..d_max; the caller draws them).  d_sets: float32 [n_sets][m][3], each
+ * set in the camera frame (camera at the origin looking along +z).  For every set
+ *   I_s = sum_i v(u_i) I_i / sigma^2,  I_i = [[P/n^2, -[u]x/n], [[u]x/n, P]]  (camera frame),
+ * with v from `model` (for a field this is what the field built from the set returns at the
+ * node the camera sits on, Eq. fim_separation), then d_metrics[s] = (trace, log|det|,
+ * lambda_min) as fif_query computes them, d_sign[s] = sign of det (optional).  No range shell
+ * is applied.  d_threshold (device float64[3], optional): the mean of each metric over the
+ * sets, only over sets with lambda_min > 1e-6 trace when exclude_degenerate (the paper's
+ * remedy for degenerate configurations), NaN when no set counts; summed in a fixed order
+ * (bitwise reproducible).  params supplies half_fov, v_alpha and sigma; gp (host struct, axes,
+ * length scale, noise, k_s; no upload needed) is required for FIF_MODEL_GP, ignored otherwise.
+ * 1 <= m; n_sets may be 0 (thresholds NaN). */
+FIF_API int32_t fif_info_threshold(const fif_params* params, int32_t model, const fif_gp* gp, const float* d_sets,
+                                   int64_t n_sets, int32_t m, int32_t exclude_degenerate, double* d_metrics,
+                                   int8_t* d_sign, double* d_threshold, fif_stream_t stream);
+
+/* Information potential cost (Eq. info_pot_cost) of metric values v (d_values[i * stride],
+ * float64, e.g. a column of fif_query's d_metrics with stride 3):
+ *   c = 0 for v > eps;  k_q (v - eps)^2 for 0 <= v <= eps;  k_l v + b_l for v < 0,
+ * with k_l = -2 k_q eps and b_l = k_q eps^2 so that c and dc/dv are continuous at v = 0
+ * (readings of the garbled equation: the middle case is taken as (v - eps)^2 and the continuity
+ * condition at v = 0).  d_cost, d_dcost: float64[m] (either may be NULL); NaN values give NaN.
+ * eps > 0, k_q > 0. */
+FIF_API int32_t fif_info_cost(const double* d_values, int64_t m, int64_t stride, double eps, double k_q,
+                              double* d_cost, double* d_dcost, fif_stream_t stream);
+
 /* Save the field to a file: a fixed header (magic, version, grid, params, storage,
  * stride, FNV-1a checksum of the payload) followed by the raw storage.  Synchronises
  * `stream` and copies through `host_staging` (at least field->bytes bytes, caller-owned;

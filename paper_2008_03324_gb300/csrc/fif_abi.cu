@@ -346,6 +346,50 @@ int32_t fif_pointcloud_fim(const float* d_landmarks, int64_t n, const fif_params
     return fif::launch_pointcloud(a, stream);
 }
 
+int32_t fif_info_threshold(const fif_params* params, int32_t model, const fif_gp* gp, const float* d_sets,
+                           int64_t n_sets, int32_t m, int32_t exclude_degenerate, double* d_metrics, int8_t* d_sign,
+                           double* d_threshold, fif_stream_t stream) {
+    int rc = check_params(params);
+    if (rc) return rc;
+    if (model < FIF_MODEL_POINTCLOUD || model > FIF_MODEL_GP || m < 1 || n_sets < 0) return FIF_EINVAL;
+    if (n_sets > 0 && (!d_sets || !d_metrics)) return FIF_EINVAL;
+    if (reinterpret_cast<uintptr_t>(d_sets) & 3u) return FIF_EALIGN;
+    fif::InfoArgs a{};
+    a.sets = d_sets;
+    a.n = n_sets;
+    a.m = m;
+    a.model = model;
+    a.inv_sigma2 = (float)(1.0 / (params->sigma * params->sigma));
+    double k[3];
+    quad_coeffs(params->half_fov, params->v_alpha, k);
+    a.k0 = (float)k[0]; a.k1 = (float)k[1]; a.k2 = (float)k[2];
+    if (model == FIF_MODEL_GP) {
+        if (!gp || !(gp->k_s > 0.0) || !std::isfinite(gp->k_s)) return FIF_EINVAL;
+        const double e3[3] = {0.0, 0.0, 1.0};
+        double w[FIF_GP_MAX_SAMPLES];
+        if ((rc = fif::gp_kriging_weights(gp, e3, w))) return rc;
+        a.gp_ns = gp->n_samples;
+        a.gp_ks = (float)gp->k_s;
+        a.gp_cos_alpha = (float)std::cos(params->half_fov);
+        for (int s = 0; s < gp->n_samples; ++s) {
+            const double* z = gp->axes[s];
+            const double nz = std::sqrt(z[0] * z[0] + z[1] * z[1] + z[2] * z[2]);
+            a.gp_a[s] = (float)w[s];
+            for (int c = 0; c < 3; ++c) a.gp_axes[s][c] = (float)(z[c] / nz);
+        }
+    }
+    a.metrics = d_metrics;
+    a.sign = d_sign;
+    return fif::launch_info_threshold(a, exclude_degenerate != 0, d_threshold, stream);
+}
+
+int32_t fif_info_cost(const double* d_values, int64_t m, int64_t stride, double eps, double k_q, double* d_cost,
+                      double* d_dcost, fif_stream_t stream) {
+    if (m < 0 || stride < 1 || (m > 0 && !d_values)) return FIF_EINVAL;
+    if (!(eps > 0.0) || !std::isfinite(eps) || !(k_q > 0.0) || !std::isfinite(k_q)) return FIF_EINVAL;
+    return fif::launch_info_cost(d_values, m, stride, eps, k_q, d_cost, d_dcost, stream);
+}
+
 int32_t fif_field_save(const fif_field* field, const char* path, void* host_staging, fif_stream_t stream) {
     int rc = check_field(field);
     if (rc) return rc;

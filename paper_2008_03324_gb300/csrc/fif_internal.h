@@ -128,6 +128,30 @@ struct PointCloudArgs {
 };
 int launch_pointcloud(const PointCloudArgs& a, cudaStream_t stream);
 
+// ---- information threshold and potential cost ---------------------------------------
+struct InfoArgs {
+    const float* sets;     // [n][m][3] camera frame
+    int64_t n;
+    int m;
+    int model;             // FIF_MODEL_*
+    float inv_sigma2;
+    float k0, k1, k2;      // quadratic visibility
+    // GP visibility at the optical axis e3: v = sum_s gp_a[s] / (1 + exp(-ks (axes[s] . u - cos_alpha)))
+    int gp_ns;
+    float gp_ks, gp_cos_alpha;
+    float gp_a[FIF_GP_MAX_SAMPLES];
+    float gp_axes[FIF_GP_MAX_SAMPLES][3];
+    double* metrics;       // [n][3]
+    int8_t* sign;          // [n] or null
+};
+int launch_info_threshold(const InfoArgs& a, int exclude, double* d_threshold, cudaStream_t stream);
+int launch_info_cost(const double* v, int64_t m, int64_t stride, double eps, double kq, double* cost, double* dcost,
+                     cudaStream_t stream);
+
+// the kriging weights a(z) = (K^s + noise I)^-1 K_z of a GP model (host, double precision);
+// FIF_EINVAL when the model is invalid or K^s + noise I is not positive definite
+int gp_kriging_weights(const fif_gp* gp, const double z[3], double* a);
+
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 }  // namespace fif

@@ -36,6 +36,7 @@
 #include "fif_common.cuh"
 #include "fif_internal.h"
 #include "landmark_stream.cuh"
+#include "bearing.cuh"
 
 #include <cmath>
 #include <cstring>
@@ -76,25 +77,6 @@ FIF_DEV float rcp_approx(float x) {
     float y;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
-}
-
-// entry e of D_g from its 15 moments m (before 1/sigma^2):
-//   TT = P/n^2, TR = -[u]x / n, RR = P with P = I - u u^T; m[0..5] = sum v (xx yy zz xy xz yz),
-//   m[6..11] the same over n^2, m[12..14] = sum v (x y z) / n
-FIF_DEV float gp_entry(int e, const float* m) {
-    const int r = sym_row(e), c = sym_col(e);
-    auto diag = [&](int base, int a) {
-        return a == 0 ? m[base + 1] + m[base + 2] : a == 1 ? m[base + 0] + m[base + 2] : m[base + 0] + m[base + 1];
-    };
-    if (r < 3 && c < 3) return r == c ? diag(6, r) : -m[6 + 2 + r + c];
-    if (r < 3) {
-        const int b = c - 3;
-        if (r == b) return 0.f;
-        const int l = 3 - r - b;
-        return ((r + 1) % 3 == b) ? m[12 + l] : -m[12 + l];
-    }
-    const int ra = r - 3, cb = c - 3;
-    return ra == cb ? diag(0, ra) : -m[2 + ra + cb];
 }
 
 template <int G>
@@ -294,7 +276,7 @@ __global__ void __launch_bounds__(kGbThreads, 1) gp_build_kernel(BuildArgs a) {
         const bool live = ok && g < a.gp_ns;
 #pragma unroll
         for (int e = 0; e < 21; ++e) {
-            float v = live ? gp_entry(e, mo) * a.inv_sigma2 : 0.f;
+            float v = live ? bearing_entry(e, mo) * a.inv_sigma2 : 0.f;
             if (a.accumulate != 0) v = fmaf((float)a.accumulate, v, out[e * rs + g]);
             out[e * rs + g] = v;
         }

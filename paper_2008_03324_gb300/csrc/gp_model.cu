@@ -100,6 +100,36 @@ double log_marginal(const double (*axes)[3], int ns, double l, double noise, con
 
 }  // namespace
 
+namespace fif {
+
+int gp_kriging_weights(const fif_gp* gp, const double z[3], double* a) {
+    if (!gp || !valid_count(gp->n_samples)) return FIF_EINVAL;
+    if (!(gp->length_scale > 0.0) || !std::isfinite(gp->length_scale)) return FIF_EINVAL;
+    if (!(gp->noise_var >= 0.0) || !std::isfinite(gp->noise_var)) return FIF_EINVAL;
+    const int ns = gp->n_samples;
+    double axes[FIF_GP_MAX_SAMPLES][3];
+    if (!normalised_axes(gp, axes)) return FIF_EINVAL;
+    std::vector<double> K;
+    kernel_matrix(axes, ns, gp->length_scale, gp->noise_var, K);
+    if (!cholesky(K, ns)) return FIF_EINVAL;
+    // a = (L L^T)^-1 k_z: forward then backward substitution
+    std::vector<double> y(ns);
+    const double s = 1.0 / (2.0 * gp->length_scale * gp->length_scale);
+    for (int g = 0; g < ns; ++g) {
+        const double d0 = z[0] - axes[g][0], d1 = z[1] - axes[g][1], d2 = z[2] - axes[g][2];
+        y[g] = std::exp(-(d0 * d0 + d1 * d1 + d2 * d2) * s);
+    }
+    forward_solve(K, ns, y.data());
+    for (int i = ns - 1; i >= 0; --i) {
+        double v = y[i];
+        for (int k = i + 1; k < ns; ++k) v -= K[(size_t)k * ns + i] * a[k];
+        a[i] = v / K[(size_t)i * ns + i];
+    }
+    return FIF_OK;
+}
+
+}  // namespace fif
+
 extern "C" {
 
 int32_t fif_gp_row_stride(int32_t ns) {

@@ -29,6 +29,7 @@ LIB_PATH = os.path.join(_HERE, "libfif.so")
 OK, EINVAL, ESIZE, EALIGN, ECUDA, ETIMEOUT, EIO, EFORMAT, ERANGE = 0, -1, -2, -3, -4, -5, -6, -7, -8
 POSE_OUTSIDE, POSE_QUAT, POSE_NOT_PD, POSE_NAN = 1, 2, 4, 8
 STORAGE_F32, STORAGE_BF16, STORAGE_TRACE, STORAGE_GP = 0, 1, 2, 3
+MODEL_POINTCLOUD, MODEL_QUAD, MODEL_GP = 0, 1, 2
 GP_MAX_SAMPLES = 96
 Q_TRILINEAR, Q_NEAREST, Q_CAMERA, Q_WORLD = 0x0, 0x1, 0x0, 0x2
 Q_TRACE, Q_LOGDET, Q_LMIN, Q_METRICS = 0x10, 0x20, 0x40, 0x70
@@ -101,6 +102,9 @@ _SIGS = {
     "fif_gp_field_bytes": (ctypes.c_size_t, [ctypes.POINTER(Grid), _I32]),
     "fif_field_init_gp": (_I32, [ctypes.POINTER(FieldC), ctypes.POINTER(Grid), ctypes.POINTER(Params),
                                  ctypes.POINTER(GPC), _VP, ctypes.c_size_t]),
+    "fif_info_threshold": (_I32, [ctypes.POINTER(Params), _I32, ctypes.POINTER(GPC), _VP, _I64, _I32, _I32, _VP, _VP,
+                                  _VP, _VP]),
+    "fif_info_cost": (_I32, [_VP, _I64, _I64, ctypes.c_double, ctypes.c_double, _VP, _VP, _VP]),
 }
 SYMBOLS = tuple(_SIGS)
 
@@ -251,6 +255,67 @@ class GPModel:
     @property
     def length_scale(self):
         return float(self.c.length_scale)
+
+
+def gp_struct(axes, length_scale, noise_var=1e-10, k_s=15.0) -> GPC:
+    """A host GP model struct (not uploaded): enough for fif_info_threshold."""
+    return _gp_struct(axes, length_scale, noise_var, k_s)
+
+
+def info_threshold(params: Params, sets: torch.Tensor, model=MODEL_POINTCLOUD, gp: GPC | None = None,
+                   exclude_degenerate=True, metrics=None, sign=None, threshold=None, stream=None):
+    """fif_info_threshold: sets [n, m, 3] camera-frame float32 -> (metrics [n, 3] float64,
+    thresholds [3] float64), both on the device."""
+    assert sets.is_cuda and sets.dtype == torch.float32 and sets.is_contiguous() and sets.dim() == 3
+    n, m = sets.shape[0], sets.shape[1]
+    if metrics is None:
+        metrics = torch.empty(n, 3, dtype=torch.float64, device=sets.device)
+    if threshold is None:
+        threshold = torch.empty(3, dtype=torch.float64, device=sets.device)
+    _check(lib().fif_info_threshold(ctypes.byref(params), int(model), ctypes.byref(gp) if gp is not None else None,
+                                    _ptr(sets), n, m, int(bool(exclude_degenerate)), _ptr(metrics), _ptr(sign),
+                                    _ptr(threshold), _stream(stream)), "fif_info_threshold")
+    return metrics, threshold
+
+
+def info_cost(values: torch.Tensor, eps: float, k_q: float, column=None, cost=None, dcost=None, stream=None):
+    """fif_info_cost of a float64 vector, or of one column of a contiguous [m, k] float64 matrix
+    (column = index).  Returns (cost, dcost) [m] float64."""
+    assert values.is_cuda and values.dtype == torch.float64 and values.is_contiguous()
+    if column is None:
+        m, stride, ptr = values.numel(), 1, values.data_ptr()
+    else:
+        m, stride = values.shape[0], values.shape[1]
+        ptr = values.data_ptr() + 8 * int(column)
+    if cost is None:
+        cost = torch.empty(m, dtype=torch.float64, device=values.device)
+    if dcost is None:
+        dcost = torch.empty(m, dtype=torch.float64, device=values.device)
+    _check(lib().fif_info_cost(ctypes.c_void_p(ptr), m, stride, float(eps), float(k_q), _ptr(cost), _ptr(dcost),
+                               _stream(stream)), "fif_info_cost")
+    return cost, dcost
+
+
+class InfoCost(torch.autograd.Function):
+    """cost = InfoCost.apply(metrics [m, 3] float64, column, eps, k_q) -> [m]: the information
+    potential cost of one metric column (Eq. info_pot_cost); backward multiplies by dc/dv from
+    the same kernel."""
+
+    @staticmethod
+    def forward(ctx, metrics, column, eps, k_q):
+        met = metrics.detach().contiguous()
+        cost, dcost = info_cost(met, eps, k_q, column=column)
+        ctx.column = column
+        ctx.save_for_backward(dcost)
+        ctx.shape = met.shape
+        return cost
+
+    @staticmethod
+    def backward(ctx, g):
+        (dcost,) = ctx.saved_tensors
+        grad = torch.zeros(ctx.shape, dtype=torch.float64, device=dcost.device)
+        grad[:, ctx.column] = (g.to(torch.float64) * dcost).nan_to_num()
+        return grad, None, None, None
 
 
 def build_workspace_bytes(field: FieldC, n: int) -> int:

@@ -44,3 +44,19 @@ def neg_logdet_objective(ctrl: torch.Tensor, yaw_ctrl: torch.Tensor, basis: torc
     mask = (sg > 0).to(met.dtype)
     loss = -(met[:, 1].nan_to_num() * mask).sum()
     return loss, phi, met, sg
+
+
+def potential_cost_objective(ctrl: torch.Tensor, yaw_ctrl: torch.Tensor, basis: torch.Tensor, field: fif.Field,
+                             eps: float, k_q: float, column: int = 1, flags: int = fif.Q_METRICS):
+    """The information potential cost (Sec. VI-B, Eq. info_pot_cost) summed over the samples:
+    loss = sum_s c(v_s), v_s = metric `column` (0 trace, 1 log|det|, 2 lambda_min) of sample s,
+    with the threshold eps from fif.info_threshold.  The cost and its derivative come from the
+    library's kernel, the metric gradient from the query adjoint.  Returns (loss, phi, met)."""
+    T, C, _ = ctrl.shape
+    t = torch.einsum("sc,tcd->tsd", basis, ctrl).reshape(-1, 3)
+    yaw = (yaw_ctrl @ basis.T).reshape(-1)
+    quat = horizontal_quats(yaw)
+    phi = torch.zeros(t.shape[0], 3, device=t.device, dtype=t.dtype, requires_grad=True)
+    met, sg, st = fif.FifQuery.apply(t.contiguous(), phi, quat.contiguous(), field, flags)
+    cost = fif.InfoCost.apply(met, column, eps, k_q)
+    return cost.sum(), phi, met
