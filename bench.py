@@ -52,6 +52,9 @@ QUERY_TRAFFIC = {"bytes_per_pose": (28.973279e9 + 0.474722e9) / 4194304,
 # (read 11.724 GB + write 0.0115 GB for 262,144 poses on the 200 x 200 x 8 lattice)
 GP_QUERY_TRAFFIC = {"bytes_per_pose": (11.724005e9 + 0.011493e9) / 262144, "n_samples": 70,
                     "digest": "c8d628ace602e5be"}
+# FMA-pipe utilisation of build_kernel (ncu sm__pipe_fma_cycles_active, profiles/build_kernel_warehouse_nz8.md),
+# valid while the build sources hash to the recorded digest
+BUILD_PIPE = {"fma_pipe_active": 0.643, "digest": "a6932fd6e7972f0b"}
 # GP build, per (in-shell pair, sample axis): sigmoid 10 (dot 6, shift 1, exp 1, add 1, rcp 1)
 # + 15 moment accumulations 30; per pair: bearing products 16
 GP_FLOPS_PER_PAIR_SAMPLE = 40
@@ -276,6 +279,67 @@ def gp_block(fif, synth, spec, lm, r_max, m, ns, dev, stream, hbm_peak, build_st
     return out
 
 
+def method_accuracy(fif, synth, dev, n_poses=200):
+    """Accuracy of the field representations against the exact point-cloud FIM (Sec. VII-A,
+    Eq. fim_rel_diff): 1000 random landmarks in a 10 x 10 x 5 m box, fields on the 9 x 9 x 4 m
+    region inside it at 0.5 m, poses at random nodes with uniform rotations, e_FIM =
+    ||I_field - I_pc||_F / ||I_pc||_F in the camera frame (the field at its own node isolates the
+    visibility model, as the paper's nearest-voxel test does).  Context for the paper's table,
+    not a parity check."""
+    import torch
+    lm = synth.random_box(8, 1000)
+    spec = synth.GridSpec((0.5, 0.5, 0.5), 0.5, (19, 19, 9))
+    rng = np.random.default_rng(9)
+    idx = rng.integers(0, spec.dims, size=(n_poses, 3))
+    q = rng.standard_normal((n_poses, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    poses = np.concatenate([np.asarray(spec.origin) + spec.res * idx, q], axis=1).astype(np.float32)
+    P = torch.from_numpy(poses).to(dev)
+    L = torch.from_numpy(lm).to(dev)
+    prm_pc = fif.make_params(r_min=0.1, r_max=30.0)
+    fim_pc = torch.empty(n_poses, 21, device=dev)
+    fif.pointcloud_fim(L, prm_pc, fif.make_pinhole(), P, 0, fim_pc, None, None, None)
+    w = torch.tensor([1.0 if r == c else 2.0 for r in range(6) for c in range(r, 6)], device=dev)
+    fro = lambda x: torch.sqrt((w * x.double() ** 2).sum(1))
+    out = {}
+    models = [("Q-I-0.5", None, 0.5), ("Q-I-0.8", None, 0.8)] + [(f"G-I-{n}", n, 0.5) for n in (30, 50, 70, 96)]
+    for name, ns, va in models:
+        prm = fif.make_params(v_alpha=va, r_min=0.1, r_max=30.0)
+        if ns is None:
+            fld = fif.Field(spec.origin, spec.res, spec.dims, prm)
+        else:
+            axes = synth.fibonacci_sphere(ns)
+            gp = fif.GPModel(axes, fif.gp_fit_length_scale(axes, synth.sphere_points(7, 2000)))
+            fld = fif.Field(spec.origin, spec.res, spec.dims, prm, storage=fif.STORAGE_GP, gp=gp)
+        fld.build(L)
+        fim, _, _, _ = fld.query(P, fif.Q_NEAREST)
+        ref = fro(fim_pc)
+        seen = (ref > 0).cpu().numpy()          # poses whose camera sees at least one landmark
+        e = (fro(fim - fim_pc) / ref.clamp_min(1e-300)).cpu().numpy()[seen]
+        out[name] = {"mean_pct": float(100 * e.mean()), "median_pct": float(100 * np.median(e)),
+                     "poses": int(seen.sum())}
+    out["paper_pct"] = {"Q-I-0.5": 64.26, "Q-I-0.8": 164.92, "G-I-30": 11.15, "G-I-50": 9.88, "G-I-70": 9.49}
+    return out
+
+
+def serving_run(fif, serve, field, reqs, rate, seed):
+    srv = serve.FifServer(field, max_batch_poses=1 << 19, slots=512, mem_budget_bytes=256 << 20, streams=2)
+    srv.run(reqs[:50], serve_arrivals(seed, 50, rate))   # warm-up
+    arr = serve_arrivals(seed + 1, len(reqs), rate)
+    t0 = time.perf_counter()
+    res = srv.run(reqs, arr)
+    wall = time.perf_counter() - t0
+    n_poses = sum(r.shape[0] for r in reqs)
+    return {"arrival_rate_req_per_s": rate, "requests": len(reqs), "poses": n_poses,
+            "served_queries_per_s": n_poses / wall, "batches": srv.batches_launched,
+            "peak_inflight_bytes": srv.peak_bytes, **serve.latency_stats(res)}
+
+
+def serve_arrivals(seed, count, rate):
+    from paper_2008_03324_gb300 import synth
+    return synth.poisson_arrivals(seed, count, rate)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -344,7 +408,10 @@ def main():
         "launches_per_build": 7,
         "roofline": {"bound": "alu", "achieved": build_tflops, "peak": nominal_fp32, "unit": "TFLOP/s",
                      "frac": build_tflops / nominal_fp32, "traffic": None,
-                     "peak_kind": "nominal FP32: 152 SMs x 128 lanes x 2 x 2070 MHz"},
+                     "peak_kind": "nominal FP32: 152 SMs x 128 lanes x 2 x 2070 MHz",
+                     "fma_pipe_active_ncu": (BUILD_PIPE["fma_pipe_active"] if BUILD_PIPE["digest"] ==
+                                             query_source_digest(("build.cu", "landmark_stream.cuh", "fif_common.cuh"))
+                                             else None)},
     }
     assert fif.device_error() == 0
     if args.phase == "build":
@@ -438,7 +505,6 @@ def main():
     out["bf16"] = {"queries_per_s": m / (ms16 * 1e-3), "kernel_ms": ms16, "bytes_per_pose": b16,
                    "roofline": {"bound": "hbm", "achieved": m * b16 / (ms16 * 1e-3) / 1e9, "peak": hbm_peak,
                                 "unit": "GB/s", "frac": m * b16 / (ms16 * 1e-3) / 1e9 / hbm_peak}}
-    del field16
     torch.cuda.empty_cache()
 
     # ---------------- positional trace factor (10 floats per node, world-frame trace) ----------------
@@ -514,6 +580,9 @@ def main():
             large[name] = {"build_ms": float(tbl[0]), "in_shell_pairs": ins, "build_pairs_per_s": ins / (tbl[0] * 1e-3),
                            "field_bytes": bf.coeffs.numel() * bf.coeffs.element_size(),
                            "queries_per_s": m / (float(np.mean(tql)) * 1e-3)}
+            if rank == 0 and args.serve_requests > 0:
+                breqs = synth.request_stream(13, min(600, args.serve_requests), bscene, zr=(0.5, 19.5))
+                large[name]["serving"] = serving_run(fif, serve, bf, breqs, 20_000.0, 14)
             del bf, bws, bposes
             torch.cuda.empty_cache()
         out["large"] = large
@@ -521,19 +590,22 @@ def main():
 
     # ---------------- serving (rank 0) ----------------
     if rank == 0 and args.serve_requests > 0:
+        # Poisson request streams at 2k-50k requests/s (8-4096 poses each) on the fp32 and bf16
+        # fields; the 20k fp32 run is the headline p99
         reqs = synth.request_stream(3, args.serve_requests, scene)
-        rate = 20_000.0
-        arr = synth.poisson_arrivals(4, len(reqs), rate)
-        srv = serve.FifServer(field, max_batch_poses=1 << 19, slots=512, mem_budget_bytes=256 << 20, streams=2)
-        srv.run(reqs[:50], synth.poisson_arrivals(5, 50, rate))   # warm-up
-        t0 = time.perf_counter()
-        res = srv.run(reqs, arr)
-        wall = time.perf_counter() - t0
-        lat = serve.latency_stats(res)
-        n_poses = sum(r.shape[0] for r in reqs)
-        out["serving"] = {"arrival_rate_req_per_s": rate, "requests": len(reqs), "poses": n_poses,
-                          "served_queries_per_s": n_poses / wall, "batches": srv.batches_launched,
-                          "peak_inflight_bytes": srv.peak_bytes, **lat}
+        sweep = {}
+        for sname, sfield, bpp in (("f32", field, 6720), ("bf16", field16, 3360)):
+            for rate in (2_000.0, 5_000.0, 10_000.0, 20_000.0, 50_000.0):
+                r = serving_run(fif, serve, sfield, reqs, rate, 4)
+                r["effective_gather_gbs"] = r["served_queries_per_s"] * bpp / 1e9
+                sweep[f"{sname}@{int(rate)}"] = r
+        out["serving"] = sweep["f32@20000"]
+        out["serving_sweep"] = {k: {kk: v[kk] for kk in ("served_queries_per_s", "p50_ms", "p99_ms",
+                                                          "effective_gather_gbs", "batches")}
+                                for k, v in sweep.items()}
+    del field16
+    if rank == 0:
+        out["method_accuracy"] = method_accuracy(fif, synth, dev)
 
     # ---------------- CPU oracle baseline (rank 0, N = 1) ----------------
     cpu = None

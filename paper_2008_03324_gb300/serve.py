@@ -15,6 +15,7 @@ The scheduler (`Scheduler`) is separate from the executor that owns the streams 
 from __future__ import annotations
 
 import time
+from collections import deque
 from dataclasses import dataclass
 
 import numpy as np
@@ -65,6 +66,11 @@ class CudaExecutor:
                 d_st=torch.empty(self.max_batch, dtype=torch.int32, device=dev),
                 event=None,
             ))
+        # numpy views of the pinned staging buffers: packing and unpacking a request is one
+        # memcpy each, without per-request tensor dispatch
+        for b in self.bufs:
+            b["np_pose"], b["np_met"] = b["h_pose"].numpy(), b["h_met"].numpy()
+            b["np_sg"], b["np_st"] = b["h_sg"].numpy(), b["h_st"].numpy()
         self.launches = 0
 
     @property
@@ -76,9 +82,10 @@ class CudaExecutor:
         torch, fif = self.torch, self.fif
         b = self.bufs[slot]
         n = 0
+        dst = b["np_pose"]
         for poses in batch:
             L = poses.shape[0]
-            b["h_pose"][n:n + L].copy_(torch.from_numpy(poses))
+            dst[n:n + L] = poses
             n += L
         s = b["stream"]
         with torch.cuda.stream(s):
@@ -98,8 +105,7 @@ class CudaExecutor:
 
     def results(self, slot: int, off: int, L: int):
         b = self.bufs[slot]
-        return (b["h_met"][off:off + L].numpy().copy(), b["h_sg"][off:off + L].numpy().copy(),
-                b["h_st"][off:off + L].numpy().copy())
+        return (b["np_met"][off:off + L].copy(), b["np_sg"][off:off + L].copy(), b["np_st"][off:off + L].copy())
 
 
 class Scheduler:
@@ -136,25 +142,27 @@ class Scheduler:
         n_req = len(requests)
         if arrivals is None:
             arrivals = np.zeros(n_req)
-        order = np.argsort(arrivals, kind="stable")
-        for r in requests:
-            if r.shape[0] > self.ex.max_batch or r.shape[0] * BYTES_PER_POSE > self.mem_budget:
-                raise AdmissionError(f"request of {r.shape[0]} poses exceeds the batch or memory limit")
+        order = np.argsort(arrivals, kind="stable").tolist()
+        arr = np.asarray(arrivals, dtype=np.float64).tolist()
+        lengths = [int(r.shape[0]) for r in requests]
+        for L in lengths:
+            if L > self.ex.max_batch or L * BYTES_PER_POSE > self.mem_budget:
+                raise AdmissionError(f"request of {L} poses exceeds the batch or memory limit")
         results = [Result(np.zeros((0, 3)), np.zeros(0, np.int8), np.zeros(0, np.int32)) for _ in range(n_req)]
         t0 = clock()
         nxt, done = 0, 0
-        waiting, ready = [], []
+        waiting, ready = deque(), deque()
         inflight = {}            # stream slot -> (request ids, offsets, launch time)
         while done < n_req:
             now = clock() - t0
-            while nxt < n_req and arrivals[order[nxt]] <= now:
-                rid = int(order[nxt])
-                results[rid].arrival = float(arrivals[rid])
+            while nxt < n_req and arr[order[nxt]] <= now:
+                rid = order[nxt]
+                results[rid].arrival = arr[rid]
                 waiting.append(rid)
                 nxt += 1
-            while waiting and self._fits(requests[waiting[0]].shape[0]):
-                rid = waiting.pop(0)
-                self._admit(requests[rid].shape[0])
+            while waiting and self._fits(lengths[waiting[0]]):
+                rid = waiting.popleft()
+                self._admit(lengths[rid])
                 results[rid].admitted = now
                 ready.append(rid)
             for slot in list(inflight):
@@ -162,7 +170,7 @@ class Scheduler:
                 if self.ex.done(slot):
                     tdone = clock() - t0
                     for rid, off in zip(rids, offs):
-                        L = requests[rid].shape[0]
+                        L = lengths[rid]
                         r = results[rid]
                         r.metrics, r.sign, r.status = self.ex.results(slot, off, L)
                         r.done = tdone
@@ -174,16 +182,16 @@ class Scheduler:
             free = [s for s in range(self.ex.n_streams) if s not in inflight]
             if ready and free:
                 rids, offs, n = [], [], 0
-                while ready and n + requests[ready[0]].shape[0] <= self.ex.max_batch:
-                    rid = ready.pop(0)
+                while ready and n + lengths[ready[0]] <= self.ex.max_batch:
+                    rid = ready.popleft()
                     rids.append(rid)
                     offs.append(n)
-                    n += requests[rid].shape[0]
+                    n += lengths[rid]
                 self.ex.launch(free[0], [requests[r] for r in rids])
                 self.batches_launched += 1
                 inflight[free[0]] = (rids, offs, clock() - t0)
             elif not inflight and not ready and not waiting and nxt < n_req:
-                dt = arrivals[order[nxt]] - (clock() - t0)
+                dt = arr[order[nxt]] - (clock() - t0)
                 if dt > 2e-4:
                     sleep(dt - 1e-4)
         return results

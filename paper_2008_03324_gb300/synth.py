@@ -439,3 +439,10 @@ def threshold_sets(seed: int, n: int, m: int, d_min: float = 0.3, d_max: float =
     ph = rng.uniform(0.0, 2.0 * math.pi, size=(n, m))
     r = np.cbrt(rng.uniform(d_min ** 3, d_max ** 3, size=(n, m)))
     return np.stack([r * st * np.cos(ph), r * st * np.sin(ph), r * ct], axis=-1).astype(np.float32)
+
+
+def random_box(seed: int = 8, n: int = 1000, size=(10.0, 10.0, 5.0)) -> np.ndarray:
+    """n landmarks uniform in a size[0] x size[1] x size[2] box at the origin (float32 [n, 3]):
+    the random-landmark environment of the paper's accuracy simulation (Sec. VII-A)."""
+    rng = _rng(seed)
+    return (rng.random((n, 3)) * np.asarray(size)).astype(np.float32)
