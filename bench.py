@@ -44,14 +44,14 @@ WORKLOAD = ("warehouse 50x50x10 m, 200k landmarks (60% box faces / 40% walls, 40
 QUERY_BYTES_PER_POSE = 8 * 210 * 4 + 7 * 4 + 21 * 4 + 3 * 8 + 1 + 4   # corners + pose + outputs
 BUILD_FLOPS_PER_PAIR = 151   # shell test 8, rsqrt 1, bearing 4, monomials 31, 66 accumulations 107
 # DRAM traffic of one query launch per pose, from the ncu capture summarised in
-# profiles/query_kernel_warehouse_4M.md (read 28.973 GB + write 0.475 GB for 4,194,304 poses),
+# profiles/query_kernel_warehouse_4M.md (read 29.018 GB + write 0.476 GB for 4,194,304 poses),
 # valid while the kernel sources hash to the recorded digest
-QUERY_TRAFFIC = {"bytes_per_pose": (28.973279e9 + 0.474722e9) / 4194304,
-                 "digest": "829209c9cbefa037"}
+QUERY_TRAFFIC = {"bytes_per_pose": (29.017812e9 + 0.475997e9) / 4194304,
+                 "digest": "88a3ac2f7f615712"}
 # the same for the GP query (N_s = 70) from profiles/gp_query_kernel_warehouse_nz8.md
-# (read 11.724 GB + write 0.0115 GB for 262,144 poses on the 200 x 200 x 8 lattice)
-GP_QUERY_TRAFFIC = {"bytes_per_pose": (11.724005e9 + 0.011493e9) / 262144, "n_samples": 70,
-                    "digest": "c8d628ace602e5be"}
+# (read 11.723 GB + write 0.0116 GB for 262,144 poses on the 200 x 200 x 8 lattice)
+GP_QUERY_TRAFFIC = {"bytes_per_pose": (11.722718e9 + 0.011555e9) / 262144, "n_samples": 70,
+                    "digest": "d96d9f5a80c0e692"}
 # FMA-pipe utilisation of build_kernel (ncu sm__pipe_fma_cycles_active, profiles/build_kernel_warehouse_nz8.md),
 # valid while the build sources hash to the recorded digest
 BUILD_PIPE = {"fma_pipe_active": 0.643, "digest": "a6932fd6e7972f0b"}

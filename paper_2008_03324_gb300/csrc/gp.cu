@@ -30,9 +30,10 @@
 //                      sums with W split into high and low parts (two-product / two-sum);
 //  contract (8 warps)  warp j streams corner j of each pose (one bulk copy of the node record
 //                      into its own ring), lane e < 21 forms w_j sum_g a_g D_g[e];
-//  metric   (1 warp)   lane = pose: moves the 8 corner matrices from their nodes to the
-//                      camera position, sums, rotates into the camera frame, and reduces to
-//                      trace / log|det| / lambda_min as the quadratic query does.
+//  metric   (2 warps)  one per buffer of the corner table, lane = pose: moves the 8 corner
+//                      matrices from their nodes to the camera position, sums, rotates into the
+//                      camera frame, and reduces to trace / log|det| / lambda_min as the
+//                      quadratic query does.
 #include "fif_common.cuh"
 #include "fif_internal.h"
 #include "landmark_stream.cuh"
@@ -290,7 +291,8 @@ __global__ void __launch_bounds__(kGbThreads, 1) gp_build_kernel(BuildArgs a) {
 // ------------------------------------------------------------------------------------
 constexpr int kGqContract = 4;                 // one warp per x-adjacent corner pair
 constexpr int kGqWeights = 8;                  // one block of kGqPB poses per group each
-constexpr int kGqWarps = kGqContract + kGqWeights + 1;
+constexpr int kGqMetric = 2;                   // metric warp m finishes the groups of table buffer m
+constexpr int kGqWarps = kGqContract + kGqWeights + kGqMetric;
 constexpr int kGqThreads = kGqWarps * 32;
 constexpr int kGqPB = 4;                       // poses per weights block
 constexpr int kEbRow = 169;                    // floats per pose in the corner table (odd)
@@ -718,7 +720,8 @@ __global__ void __launch_bounds__(kGqThreads, 1) gp_query_kernel(QueryArgs a, Gq
         }
     } else {
         // ================================ metric warp ================================
-        for (int64_t k = 0;; ++k) {
+        const int mw = warp - kGqContract - kGqWeights;   // = the table buffer it serves
+        for (int64_t k = mw;; k += kGqMetric) {
             const int64_t g = (int64_t)blockIdx.x + k * gridDim.x;
             if (g >= groups || *flag) break;
             const int b = (int)(k & 1);

@@ -66,9 +66,11 @@ __device__ __forceinline__ int mom_slot(int e, int j) {
 
 // ---- warp-specialised kernel ----------------------------------------------------------
 // kGather gather warps stream corners and assemble T; kMetric metric warps finish poses.
-// Metric warp m serves gather warps m and m + kMetric (two slots each, double-buffered).
-constexpr int kGather = 6;     // default number of gather warps per CTA
-constexpr int kMetric = 3;     // default number of metric warps per CTA
+// Metric warp m serves gather warps m, m + kMetric, ... (kGather / kMetric of them; two
+// slots each, double-buffered).  Every bounded wait that runs out sets a shared abort flag
+// that all warps of the CTA see, so the CTA leaves as a whole (after draining its copies).
+constexpr int kGather = 6;     // gather warps per CTA of the float32 configuration
+constexpr int kMetric = 6;     // metric warps per CTA of the float32 configuration
 constexpr int kRow = 33;              // floats per pose in a slot (odd stride: no bank conflicts)
 // slot row: [0..20] T (about the base node, world axes), [21..23] t, [24..27] q,
 //           [28..30] c0, [31] status bits
@@ -149,7 +151,11 @@ __global__ void __launch_bounds__((NG + NM) * 32, 1) query_kernel(QueryArgs args
     constexpr int kGB = gather_smem_bytes<kElem, NS>();
     const int64_t groups = (args.m + 31) / 32;
     const int64_t ngather = (int64_t)gridDim.x * kGather;
+    // set when a bounded wait runs out: every warp then leaves its loop (after waiting, with a
+    // short bound, for its own bulk copies still in flight)
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem_raw + kGather * kGB);
 
+    if (threadIdx.x == 0) *abort_flag = 0;
     if (threadIdx.x < kGather) {
         GS& G = *reinterpret_cast<GS*>(smem_raw + threadIdx.x * kGB);
         for (int s = 0; s < kStages; ++s) mbar_init(&G.bars[s], 4);
@@ -184,7 +190,11 @@ __global__ void __launch_bounds__((NG + NM) * 32, 1) query_kernel(QueryArgs args
         for (int64_t g = (int64_t)blockIdx.x * kGather + warp; g < groups; g += ngather, ++k) {
             const int sl = k & 1;
             const uint32_t use = (uint32_t)(k >> 1);
-            if (!mbar_wait_bounded(&G.empty[sl], (use & 1u) ^ 1u)) set_error(args.err, FIF_ETIMEOUT);
+            if (__any_sync(0xffffffffu, *abort_flag != 0 || !mbar_wait_bounded(&G.empty[sl], (use & 1u) ^ 1u))) {
+                set_error(args.err, FIF_ETIMEOUT);
+                *abort_flag = 1;
+                break;
+            }
             float* slot = G.slot[sl];
             const int64_t p0 = g * 32;
             const int cnt = (int)(args.m - p0 < 32 ? args.m - p0 : 32);
@@ -272,6 +282,7 @@ __global__ void __launch_bounds__((NG + NM) * 32, 1) query_kernel(QueryArgs args
                 }
             }
             // ---- phase G: warp per pose ----
+            bool dead = false;
             for (int i = 0; i < cnt; ++i) {
                 const int s = i % kStages;
                 if (lane < 4) {
@@ -286,7 +297,18 @@ __global__ void __launch_bounds__((NG + NM) * 32, 1) query_kernel(QueryArgs args
                     const int ipf = i + kStages - 1 + kPrefetch;
                     if (ipf < cnt) bulk_prefetch_l2(pair_src(base_of(ipf), lane), L::kPairBytes);
                 }
-                if (!mbar_wait_bounded(&G.bars[s], (phase_bits >> s) & 1u)) set_error(args.err, FIF_ETIMEOUT);
+                if (__any_sync(0xffffffffu, !mbar_wait_bounded(&G.bars[s], (phase_bits >> s) & 1u))) {
+                    set_error(args.err, FIF_ETIMEOUT);
+                    *abort_flag = 1;
+                    // the copies of poses i .. i + kStages - 1 may still be in flight
+                    if (lane == 0)
+                        for (int r = i; r < min(cnt, i + kStages); ++r)
+                            mbar_wait_bounded(&G.bars[r % kStages], ((phase_bits >> (r % kStages)) & 1u) ^
+                                                                        (r - i >= kStages ? 1u : 0u),
+                                              100000000ull);
+                    dead = true;
+                    break;
+                }
                 phase_bits ^= (1u << s);
                 const PoseEntry& pe = G.ptab[i];
                 const float wj = (bx ? pe.w[0] : 1.f - pe.w[0]) * (by ? pe.w[1] : 1.f - pe.w[1]) *
@@ -325,6 +347,7 @@ __global__ void __launch_bounds__((NG + NM) * 32, 1) query_kernel(QueryArgs args
                 }
                 __syncwarp();
             }
+            if (dead) break;
             fence_proxy_async();
             if (lane == 0) mbar_arrive(&G.full[sl]);
         }
@@ -332,7 +355,8 @@ __global__ void __launch_bounds__((NG + NM) * 32, 1) query_kernel(QueryArgs args
         // =============================== metric warp ===============================
         const int mw = warp - kGather;
         int k = 0;
-        for (;; ++k) {
+        bool dead = false;
+        for (; !dead; ++k) {
             bool any = false;
 #pragma unroll 1
             for (int h = 0; h < kGather / kMetric; ++h) {
@@ -343,7 +367,12 @@ __global__ void __launch_bounds__((NG + NM) * 32, 1) query_kernel(QueryArgs args
                 GS& G = *reinterpret_cast<GS*>(smem_raw + gw * kGB);
                 const int sl = k & 1;
                 const uint32_t use = (uint32_t)(k >> 1);
-                if (!mbar_wait_bounded(&G.full[sl], use & 1u)) set_error(args.err, FIF_ETIMEOUT);
+                if (__any_sync(0xffffffffu, *abort_flag != 0 || !mbar_wait_bounded(&G.full[sl], use & 1u))) {
+                    set_error(args.err, FIF_ETIMEOUT);
+                    *abort_flag = 1;
+                    dead = true;
+                    break;
+                }
                 const float* slot = G.slot[sl];
                 const int64_t p0 = g * 32;
                 const int cnt = (int)(args.m - p0 < 32 ? args.m - p0 : 32);
@@ -436,7 +465,7 @@ __global__ void __launch_bounds__((NG + NM) * 32, 1) query_kernel(QueryArgs args
 template <int kElem, int NG, int NM, int NS, int NP>
 int launch_query_cfg(const QueryArgs& a, cudaStream_t stream) {
     auto kern = query_kernel<kElem, NG, NM, NS, NP>;
-    const int smem = NG * gather_smem_bytes<kElem, NS>();
+    const int smem = NG * gather_smem_bytes<kElem, NS>() + 16;   // + the abort flag
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return FIF_ECUDA;
     int dev = 0, sms = 0;
@@ -452,7 +481,7 @@ int launch_query_cfg(const QueryArgs& a, cudaStream_t stream) {
 
 int launch_query(const QueryArgs& a, cudaStream_t stream) {
     if (a.storage == FIF_STORAGE_BF16) return launch_query_cfg<2, 8, 4, 3, 4>(a, stream);
-    return launch_query_cfg<4, kGather, kMetric, kStages, kPrefetch>(a, stream);
+    return launch_query_cfg<4, 6, 6, kStages, kPrefetch>(a, stream);
 }
 
 }  // namespace fif

@@ -26,7 +26,7 @@ def uploaded_room_field(F, v_alpha=0.5, storage=0):
     spec = X.ROOM["grid"]
     field = F.Field(spec.origin, spec.res, spec.dims, F.make_params(r_max=X.ROOM["r_max"], v_alpha=v_alpha),
                     storage=storage)
-    buf = X.pack_field(X.room_field_oracle(True))
+    buf = X.pack_field(X.room_field_oracle(True), stride=field.coeffs.shape[1])
     field.coeffs.copy_(torch.from_numpy(buf).to(field.coeffs.dtype))
     return field
 
@@ -163,3 +163,22 @@ def test_bf16_build_and_query_vs_fp64_oracle(F):
     fim, met, sg, st = run(F, field, poses)
     I_ref, _ = oracle_query(poses)
     assert X.rel_fro(X.unpack21(fim), I_ref).max() <= X.TAU_BF16
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_metrics_of_the_returned_fim(F, storage):
+    """The metric arithmetic alone: log|det|, its sign and lambda_min of the FIM the kernel
+    returned (read back as float32 and evaluated in FP64 by the oracle) agree to double
+    precision -- log|det| within 1e-12 ||I|| ||I^-1|| + 5e-7, lambda_min within 1e-7 ||I||
+    (single-precision Jacobi eigenvector, double-precision Rayleigh quotient)."""
+    field = uploaded_room_field(F, storage=storage)
+    fim, met, sg, st = run(F, field, X.room_poses(1000))
+    I = X.unpack21(fim)
+    mo = O.metrics(I)
+    n = X.fro(I)
+    inv = np.array([X.fro(np.linalg.pinv(M)) for M in I])
+    ok = mo[:, 2] != 0
+    assert np.all(np.abs(met[ok, 1] - mo[ok, 1]) <= 1e-12 * n[ok] * inv[ok] + 5e-7)
+    np.testing.assert_array_equal(sg[ok], mo[ok, 2].astype(np.int8))
+    assert np.all(np.abs(met[:, 2] - mo[:, 3]) <= 1e-7 * n)
+    assert np.all(np.abs(met[:, 0] - np.trace(I, axis1=1, axis2=2)) <= 1e-6 * n)
