@@ -47,14 +47,14 @@ BUILD_FLOPS_PER_PAIR = 151   # shell test 8, rsqrt 1, bearing 4, monomials 31, 6
 # profiles/query_kernel_warehouse_4M.md (read 29.018 GB + write 0.476 GB for 4,194,304 poses),
 # valid while the kernel sources hash to the recorded digest
 QUERY_TRAFFIC = {"bytes_per_pose": (29.017812e9 + 0.475997e9) / 4194304,
-                 "digest": "88a3ac2f7f615712"}
+                 "digest": "e7fad0a4b4702022"}
 # the same for the GP query (N_s = 70) from profiles/gp_query_kernel_warehouse_nz8.md
 # (read 11.723 GB + write 0.0116 GB for 262,144 poses on the 200 x 200 x 8 lattice)
 GP_QUERY_TRAFFIC = {"bytes_per_pose": (11.722718e9 + 0.011555e9) / 262144, "n_samples": 70,
-                    "digest": "d96d9f5a80c0e692"}
+                    "digest": "72d025933a00cc55"}
 # FMA-pipe utilisation of build_kernel (ncu sm__pipe_fma_cycles_active, profiles/build_kernel_warehouse_nz8.md),
 # valid while the build sources hash to the recorded digest
-BUILD_PIPE = {"fma_pipe_active": 0.643, "digest": "a6932fd6e7972f0b"}
+BUILD_PIPE = {"fma_pipe_active": 0.643, "digest": "47fe25de634907bf"}
 # GP build, per (in-shell pair, sample axis): sigmoid 10 (dot 6, shift 1, exp 1, add 1, rcp 1)
 # + 15 moment accumulations 30; per pair: bearing products 16
 GP_FLOPS_PER_PAIR_SAMPLE = 40
@@ -65,11 +65,17 @@ SM_MAX_MHZ = 2070.0
 
 
 def query_source_digest(files=("query.cu", "gather.cuh", "fif_common.cuh")):
+    """Hash of the kernel sources with // comments and blank lines removed (a comment edit
+    leaves the recorded counters valid; any code change invalidates them)."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in files:
-        with open(os.path.join(ROOT, "paper_2008_03324_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2008_03324_gb300", "csrc", f)) as fh:
+            for line in fh:
+                code = re.sub(r"//.*", "", line).rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 
