@@ -294,6 +294,28 @@ FIF_API int32_t fif_query(const fif_field* field, const float* d_poses, int64_t 
                   float* d_fim, double* d_metrics, int8_t* d_sign, int32_t* d_status,
                   fif_stream_t stream);
 
+/* Bytes of device staging fif_query_host() needs for chunks of `chunk` poses: two buffers,
+ * each holding a chunk's poses and every output (141 B per pose, each array 256-B aligned).
+ * 0 when chunk <= 0. */
+FIF_API size_t fif_query_host_staging_bytes(int64_t chunk);
+
+/* fif_query over HOST buffers.  h_poses (float32[m][7]) and the outputs h_fim, h_metrics,
+ * h_sign, h_status (layouts and NULL meaning as for fif_query) are host memory; page-locked
+ * memory lets the copies run asynchronously and overlap the queries.  The poses go through
+ * the device in chunks of `chunk` poses, double-buffered in d_staging (caller-owned, at least
+ * fif_query_host_staging_bytes(chunk) bytes, 16-byte aligned): chunk c's host-to-device copy
+ * and chunk c-1's device-to-host copy run on copy_stream while chunk c-1 or c is queried on
+ * `stream`, ordered by events (created and released inside the call); the first copy waits for
+ * the work already queued on `stream`.  Each pose's results are
+ * those fif_query gives it.  Asynchronous: the host outputs are complete once `stream` has
+ * completed (it waits for the last copy); h_poses and the outputs must stay valid until then.
+ * copy_stream must differ from stream (FIF_EINVAL otherwise).  m = 0 returns FIF_OK and
+ * touches nothing. */
+FIF_API int32_t fif_query_host(const fif_field* field, const float* h_poses, int64_t m, int32_t flags,
+                               float* h_fim, double* h_metrics, int8_t* h_sign, int32_t* h_status,
+                               int64_t chunk, void* d_staging, size_t staging_bytes, fif_stream_t stream,
+                               fif_stream_t copy_stream);
+
 /* Adjoint of fif_query for the metrics (FIF_Q_CAMERA or FIF_Q_WORLD, trilinear):
  *   d_grad_pose[i] = sum_c d_grad_metrics[i][c] * d metric_c(T_i) / d(t, phi)
  * with t the world position and phi a right (camera-frame) so(3) perturbation

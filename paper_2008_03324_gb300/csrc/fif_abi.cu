@@ -1,5 +1,6 @@
 // fif_abi.cu -- the extern "C" entry points declared in include/fif.h: argument checks,
 // launch configuration, field files and the device error word.  No device allocation.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -292,6 +293,104 @@ int32_t fif_query(const fif_field* field, const float* d_poses, int64_t m, int32
         return fif::launch_gp_query(a, stream);
     }
     return fif::launch_query(a, stream);
+}
+
+namespace {
+
+// staging of one buffer of fif_query_host: poses, fim, metrics, sign, status (256-B aligned)
+struct HostStaging {
+    size_t poses, fim, metrics, sign, status, total;
+};
+
+HostStaging host_staging(int64_t chunk) {
+    auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+    HostStaging L;
+    size_t off = 0;
+    const size_t c = (size_t)chunk;
+    L.poses = off;   off += up(c * 7 * sizeof(float));
+    L.fim = off;     off += up(c * 21 * sizeof(float));
+    L.metrics = off; off += up(c * 3 * sizeof(double));
+    L.sign = off;    off += up(c);
+    L.status = off;  off += up(c * sizeof(int32_t));
+    L.total = off;
+    return L;
+}
+
+}  // namespace
+
+size_t fif_query_host_staging_bytes(int64_t chunk) {
+    if (chunk <= 0) return 0;
+    return 2 * host_staging(chunk).total;
+}
+
+int32_t fif_query_host(const fif_field* field, const float* h_poses, int64_t m, int32_t flags, float* h_fim,
+                       double* h_metrics, int8_t* h_sign, int32_t* h_status, int64_t chunk, void* d_staging,
+                       size_t staging_bytes, fif_stream_t stream, fif_stream_t copy_stream) {
+    int rc = check_field(field);
+    if (rc) return rc;
+    if (m < 0 || (m > 0 && !h_poses)) return FIF_EINVAL;
+    if (m == 0) return FIF_OK;
+    if (chunk <= 0 || !d_staging || stream == copy_stream) return FIF_EINVAL;
+    if (staging_bytes < fif_query_host_staging_bytes(chunk)) return FIF_ESIZE;
+    if (reinterpret_cast<uintptr_t>(d_staging) & 15u) return FIF_EALIGN;
+    const HostStaging L = host_staging(chunk);
+    unsigned char* base[2] = {static_cast<unsigned char*>(d_staging),
+                              static_cast<unsigned char*>(d_staging) + L.total};
+    cudaStream_t sq = reinterpret_cast<cudaStream_t>(stream), sc = reinterpret_cast<cudaStream_t>(copy_stream);
+    cudaEvent_t h2d[2] = {nullptr, nullptr}, qd[2] = {nullptr, nullptr}, done = nullptr, start = nullptr;
+    bool ok = cudaEventCreateWithFlags(&start, cudaEventDisableTiming) == cudaSuccess;
+    // the copies start after the work already queued on `stream`
+    ok = ok && cudaEventRecord(start, sq) == cudaSuccess && cudaStreamWaitEvent(sc, start, 0) == cudaSuccess;
+    for (int b = 0; b < 2; ++b) {
+        ok = ok && cudaEventCreateWithFlags(&h2d[b], cudaEventDisableTiming) == cudaSuccess;
+        ok = ok && cudaEventCreateWithFlags(&qd[b], cudaEventDisableTiming) == cudaSuccess;
+    }
+    ok = ok && cudaEventCreateWithFlags(&done, cudaEventDisableTiming) == cudaSuccess;
+    const int64_t nch = (m + chunk - 1) / chunk;
+    auto count = [&](int64_t c) { return std::min<int64_t>(chunk, m - c * chunk); };
+    auto upload = [&](int64_t c) {
+        const int b = (int)(c & 1);
+        ok = ok && cudaMemcpyAsync(base[b] + L.poses, h_poses + c * chunk * 7, (size_t)count(c) * 7 * sizeof(float),
+                                   cudaMemcpyHostToDevice, sc) == cudaSuccess;
+        ok = ok && cudaEventRecord(h2d[b], sc) == cudaSuccess;
+    };
+    // copy stream: H2D(0), H2D(1), D2H(0), H2D(2), D2H(1), ...; a buffer's poses are overwritten
+    // only after the query that read them (D2H of that chunk waited for it and precedes in order),
+    // and its outputs only after their D2H (the next query of the buffer waits for its H2D)
+    if (ok) upload(0);
+    for (int64_t c = 0; c < nch && ok; ++c) {
+        const int b = (int)(c & 1);
+        const int64_t n = count(c), p0 = c * chunk;
+        unsigned char* B = base[b];
+        ok = cudaStreamWaitEvent(sq, h2d[b], 0) == cudaSuccess;
+        if (!ok) break;
+        rc = fif_query(field, reinterpret_cast<const float*>(B + L.poses), n, flags,
+                       h_fim ? reinterpret_cast<float*>(B + L.fim) : nullptr,
+                       h_metrics ? reinterpret_cast<double*>(B + L.metrics) : nullptr,
+                       h_sign ? reinterpret_cast<int8_t*>(B + L.sign) : nullptr,
+                       h_status ? reinterpret_cast<int32_t*>(B + L.status) : nullptr, stream);
+        if (rc != FIF_OK) break;
+        ok = cudaEventRecord(qd[b], sq) == cudaSuccess;
+        if (ok && c + 1 < nch) upload(c + 1);
+        ok = ok && cudaStreamWaitEvent(sc, qd[b], 0) == cudaSuccess;
+        auto down = [&](void* dst, size_t off, size_t bytes) {
+            if (dst) ok = ok && cudaMemcpyAsync(dst, B + off, bytes, cudaMemcpyDeviceToHost, sc) == cudaSuccess;
+        };
+        down(h_fim ? h_fim + p0 * 21 : nullptr, L.fim, (size_t)n * 21 * sizeof(float));
+        down(h_metrics ? h_metrics + p0 * 3 : nullptr, L.metrics, (size_t)n * 3 * sizeof(double));
+        down(h_sign ? h_sign + p0 : nullptr, L.sign, (size_t)n);
+        down(h_status ? h_status + p0 : nullptr, L.status, (size_t)n * sizeof(int32_t));
+    }
+    // the query stream completes after the last copy, also on an error after work was queued
+    if (done && cudaEventRecord(done, sc) == cudaSuccess) cudaStreamWaitEvent(sq, done, 0);
+    for (int b = 0; b < 2; ++b) {
+        if (h2d[b]) cudaEventDestroy(h2d[b]);
+        if (qd[b]) cudaEventDestroy(qd[b]);
+    }
+    if (done) cudaEventDestroy(done);
+    if (start) cudaEventDestroy(start);
+    if (rc != FIF_OK) return rc;
+    return ok ? FIF_OK : FIF_ECUDA;
 }
 
 int32_t fif_query_backward(const fif_field* field, const float* d_poses, int64_t m, int32_t flags,

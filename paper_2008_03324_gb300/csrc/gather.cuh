@@ -45,12 +45,12 @@ struct Layout<2> {
 };
 
 
-__device__ __forceinline__ constexpr int sym3_idx(int r, int c) {
+__host__ __device__ constexpr int sym3_idx(int r, int c) {
     return (r <= c) ? (r * 3 - (r * (r - 1)) / 2 + (c - r)) : (c * 3 - (c * (c - 1)) / 2 + (r - c));
 }
 
 // K_a = [e_a]x
-__device__ __forceinline__ float kx(int a, int r, int c) {
+__host__ __device__ inline float kx(int a, int r, int c) {
     const float e[3] = {a == 0 ? 1.f : 0.f, a == 1 ? 1.f : 0.f, a == 2 ? 1.f : 0.f};
     const float S[3][3] = {{0.f, -e[2], e[1]}, {e[2], 0.f, -e[0]}, {-e[1], e[0], 0.f}};
     return S[r][c];

@@ -22,14 +22,19 @@
 // time, compacts the in-shell ones (u, 1/n) into a list, and every lane then accumulates, for
 // its sample axes g = lane + 32 k, the 15 moments
 //   sum v_g u_a u_b,  sum v_g u_a u_b / n^2,  sum v_g u_a / n
-// from which all 21 entries of D_g follow (|u| = 1: 1 - u_a^2 = u_b^2 + u_c^2).  Blocks of
-// about 64 pairs are summed in registers and merged into Kahan pairs in shared memory.
+// from which all 21 entries of D_g follow (|u| = 1: 1 - u_a^2 = u_b^2 + u_c^2).  When the last
+// slot of 32 axes holds r <= 16 samples, it takes q = 32 / r landmarks per pass instead of one
+// (lane l: axis 32 k + l mod r, landmark l / r), and the epilogue adds the q partial sums of an
+// axis in a fixed order; at N_s = 70 this removes the 26 idle lanes of the third slot.  Blocks
+// of about 64 pairs are summed in registers and merged into Kahan pairs in shared memory.
 //
 // Query (gp_query_kernel): a persistent CTA walks groups of 32 poses with three warp roles:
-//  weights  (4 warps)  K_z in double precision, a(z) = W K_z as compensated single-precision
-//                      sums with W split into high and low parts (two-product / two-sum);
-//  contract (8 warps)  warp j streams corner j of each pose (one bulk copy of the node record
-//                      into its own ring), lane e < 21 forms w_j sum_g a_g D_g[e];
+//  contract (4 warps)  warp p streams the x-adjacent corner pair p of each pose (one bulk copy
+//                      of both node records into its own ring), lane e < 21 forms
+//                      w_j sum_g a_g D_g[e] for both corners;
+//  weights  (8 warps)  K_z in double-float arithmetic, a(z) = W K_z as compensated
+//                      single-precision sums with W split into high and low parts
+//                      (two-product / two-sum);
 //  metric   (2 warps)  one per buffer of the corner table, lane = pose: moves the 8 corner
 //                      matrices from their nodes to the camera position, sums, rotates into the
 //                      camera frame, and reduces to trace / log|det| / lambda_min as the
@@ -124,11 +129,17 @@ __global__ void __launch_bounds__(kGbThreads, 1) gp_build_kernel(BuildArgs a) {
         for (int s = 0; s < kGbSlots; ++s) produce(s);
     }
 
+    // samples in the last slot of 32 axes, and landmarks it takes per pass (lane l of that slot:
+    // axis 32 (G - 1) + l mod rr, landmark l / rr of the pass; lanes with l / rr >= qq idle)
+    const int rr = a.gp_ns - 32 * (G - 1);
+    const int qq = (rr <= 16) ? 32 / rr : 1;
+    const int jq = lane / rr;
+    const bool main_slots = G > 1 || qq == 1;   // some slot takes one landmark per pass
     // this lane's sample axes, scaled and negated so that v = 1 / (1 + 2^(shift + nz.u))
     float nzx[G], nzy[G], nzz[G];
 #pragma unroll
     for (int k = 0; k < G; ++k) {
-        const int g = lane + 32 * k;
+        const int g = (k == G - 1 && qq > 1) ? 32 * k + lane % rr : lane + 32 * k;
         float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
         if (g < a.gp_ns) z = a.gp_axes[g];
         nzx[k] = -z.x * a.gp_scale;
@@ -162,6 +173,7 @@ __global__ void __launch_bounds__(kGbThreads, 1) gp_build_kernel(BuildArgs a) {
         }
     };
     // v_g of the bearing (x, y, z) for every owned sample axis, two axes per packed step
+    // (the last slot's value is unused when that slot runs in its own loop)
     auto sigmoids = [&](float x, float y, float z, float* v) {
 #pragma unroll
         for (int k = 0; k + 1 < G; k += 2) {
@@ -173,7 +185,7 @@ __global__ void __launch_bounds__(kGbThreads, 1) gp_build_kernel(BuildArgs a) {
             v[k] = rcp_approx(d.x);
             v[k + 1] = rcp_approx(d.y);
         }
-        if (G & 1) {
+        if ((G & 1) && qq == 1) {
             const int k = G - 1;
             const float arg = fmaf(nzx[k], x, fmaf(nzy[k], y, fmaf(nzz[k], z, shift)));
             v[k] = rcp_approx(1.f + ex2_approx(fminf(arg, 60.f)));
@@ -217,8 +229,8 @@ __global__ void __launch_bounds__(kGbThreads, 1) gp_build_kernel(BuildArgs a) {
                 }
                 __syncwarp();
                 const int nin = __popc(mask);
-#pragma unroll 1
-                for (int l = 0; l < nin; ++l) {
+#pragma unroll 2
+                for (int l = 0; l < (main_slots ? nin : 0); ++l) {
                     const float4 L = list[l];
                     const float x = L.x, y = L.y, z = L.z, in_ = L.w, w2 = L.w * L.w;
                     const float2 xy = make_float2(x, y);
@@ -233,10 +245,37 @@ __global__ void __launch_bounds__(kGbThreads, 1) gp_build_kernel(BuildArgs a) {
                     sigmoids(x, y, z, v);
 #pragma unroll
                     for (int k = 0; k < G; ++k) {
+                        if (k == G - 1 && qq > 1) break;
                         const float2 vv = make_float2(v[k], v[k]);
 #pragma unroll
                         for (int q = 0; q < 7; ++q) acc[k][q] = fma2(vv, X[q], acc[k][q]);
                         accz[k] = fmaf(v[k], zi, accz[k]);
+                    }
+                }
+                // the last slot, qq landmarks per pass
+                if (qq > 1) {
+                    constexpr int k = G - 1;
+#pragma unroll 2
+                    for (int l0 = 0; l0 < nin; l0 += qq) {
+                        const int li = l0 + jq;
+                        const bool act = jq < qq && li < nin;   // idle lanes add zero weights
+                        {
+                            const float4 L = list[act ? li : 0];
+                            const float x = L.x, y = L.y, z = L.z, in_ = L.w, w2 = L.w * L.w;
+                            const float2 xy = make_float2(x, y);
+                            const float2 m0 = mul2(xy, xy);
+                            const float2 m1 = mul2(make_float2(z, x), make_float2(z, y));
+                            const float2 m2 = mul2(xy, make_float2(z, z));
+                            const float2 ww = make_float2(w2, w2);
+                            const float2 X[7] = {m0, m1, m2, mul2(m0, ww), mul2(m1, ww), mul2(m2, ww),
+                                                 mul2(xy, make_float2(in_, in_))};
+                            const float arg = fmaf(nzx[k], x, fmaf(nzy[k], y, fmaf(nzz[k], z, shift)));
+                            const float vk = act ? rcp_approx(1.f + ex2_approx(fminf(arg, 60.f))) : 0.f;
+                            const float2 vv = make_float2(vk, vk);
+#pragma unroll
+                            for (int q = 0; q < 7; ++q) acc[k][q] = fma2(vv, X[q], acc[k][q]);
+                            accz[k] = fmaf(vk, z * in_, accz[k]);
+                        }
                     }
                 }
                 __syncwarp();
@@ -255,6 +294,7 @@ __global__ void __launch_bounds__(kGbThreads, 1) gp_build_kernel(BuildArgs a) {
         }
     }
     if (valid && inblock > 0) merge();
+    __syncwarp();
     {
         unsigned long long* stats = reinterpret_cast<unsigned long long*>(a.ws + a.lay.stats);
         if (valid && lane == 0) {
@@ -272,8 +312,20 @@ __global__ void __launch_bounds__(kGbThreads, 1) gp_build_kernel(BuildArgs a) {
         const int g = lane + 32 * k;
         if (g >= rs) continue;
         float mo[kGbMom];
+        if (k == G - 1 && qq > 1) {
+            // the qq partial sums of axis g (lanes j rr + lane), in lane order
 #pragma unroll
-        for (int m = 0; m < kGbMom; ++m) mo[m] = hw[(k * kGbMom + m) * 32] - lw[(k * kGbMom + m) * 32];
+            for (int m = 0; m < kGbMom; ++m) {
+                float t = 0.f;
+                if (lane < rr)
+                    for (int j = 0; j < qq; ++j)
+                        t += hw[(k * kGbMom + m) * 32 + j * rr] - lw[(k * kGbMom + m) * 32 + j * rr];
+                mo[m] = t;
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < kGbMom; ++m) mo[m] = hw[(k * kGbMom + m) * 32] - lw[(k * kGbMom + m) * 32];
+        }
         const bool live = ok && g < a.gp_ns;
 #pragma unroll
         for (int e = 0; e < 21; ++e) {

@@ -98,46 +98,79 @@ constexpr int gather_smem_bytes() {
 //   T_TT = A^0,  T_TR = B^0 - res sum_a A^a K_a,
 //   T_RR = D^0 - res (L + L^T) + res^2 Q,  L = sum_a K_a^T B^a,  Q = sum_ab K_a^T A^{ab} K_b,
 // K_a = [e_a]x, A^{ab} the superset sum of corners with bits a and b set (A^{aa} = A^a).
-// t_term returns term number u (the enumeration order is fixed); called once per lane.
-__device__ void t_term(int e, float res, int u, int& idx_out, float& coef_out) {
-    int n = 0;
-    idx_out = 0;
-    coef_out = 0.f;
-    auto add = [&](int idx, float c) {
-        if (c == 0.f) return;
-        if (n == u) { idx_out = idx; coef_out = c; }
-        ++n;
-    };
-    auto A = [&](int m, int r, int c) { return m * 6 + sym3_idx(r, c); };
-    auto B = [&](int ms, int r, int c) { return 42 + ms * 9 + r * 3 + c; };
-    auto D = [&](int r, int c) { return 78 + sym3_idx(r, c); };
-    const int R = sym_row(e), C = sym_col(e);
-    if (R < 3 && C < 3) {
-        add(A(0, R, C), 1.f);
-    } else if (R < 3) {
-        const int r = R, c = C - 3;
-        add(B(0, r, c), 1.f);
-        for (int a = 0; a < 3; ++a)
-            for (int l = 0; l < 3; ++l) add(A(1 << a, r, l), -res * kx(a, l, c));
-    } else {
-        const int r = R - 3, c = C - 3;
-        add(D(r, c), 1.f);
-        for (int a = 0; a < 3; ++a)
-            for (int l = 0; l < 3; ++l) {
-                add(B(a + 1, l, c), -res * kx(a, l, r));
-                add(B(a + 1, l, r), -res * kx(a, l, c));
+// The nonzero terms of entry e (at most 9) in a fixed enumeration order: term u adds
+// sgn_u * res^pw_u * mom[idx_u].  Which terms are nonzero does not depend on res (> 0), so the
+// shape is enumerated once on the host and each launch passes the table with res applied
+// (computed on the device per lane, the enumeration's cold code cost ~15-100 us per launch).
+struct TermShape {
+    int16_t idx[21][9];
+    int8_t sgn[21][9];
+    int8_t pw[21][9];
+};
+
+struct TermTable {
+    float coef[21][9];
+    int16_t idx[21][9];
+};
+
+TermShape make_term_shape() {
+    TermShape S{};
+    for (int e = 0; e < 21; ++e) {
+        int n = 0;
+        auto add = [&](int idx, float sgn, int pw) {
+            if (sgn == 0.f) return;
+            if (n < 9) {
+                S.idx[e][n] = (int16_t)idx;
+                S.sgn[e][n] = (int8_t)(sgn > 0.f ? 1 : -1);
+                S.pw[e][n] = (int8_t)pw;
             }
-        for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b)
-                for (int l = 0; l < 3; ++l)
-                    for (int m = 0; m < 3; ++m) add(A((1 << a) | (1 << b), l, m), res * res * kx(a, l, r) * kx(b, m, c));
+            ++n;
+        };
+        auto A = [](int m, int r, int c) { return m * 6 + sym3_idx(r, c); };
+        auto B = [](int ms, int r, int c) { return 42 + ms * 9 + r * 3 + c; };
+        auto D = [](int r, int c) { return 78 + sym3_idx(r, c); };
+        const int R = sym_row(e), C = sym_col(e);
+        if (R < 3 && C < 3) {
+            add(A(0, R, C), 1.f, 0);
+        } else if (R < 3) {
+            const int r = R, c = C - 3;
+            add(B(0, r, c), 1.f, 0);
+            for (int a = 0; a < 3; ++a)
+                for (int l = 0; l < 3; ++l) add(A(1 << a, r, l), -kx(a, l, c), 1);
+        } else {
+            const int r = R - 3, c = C - 3;
+            add(D(r, c), 1.f, 0);
+            for (int a = 0; a < 3; ++a)
+                for (int l = 0; l < 3; ++l) {
+                    add(B(a + 1, l, c), -kx(a, l, r), 1);
+                    add(B(a + 1, l, r), -kx(a, l, c), 1);
+                }
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b)
+                    for (int l = 0; l < 3; ++l)
+                        for (int m = 0; m < 3; ++m) add(A((1 << a) | (1 << b), l, m), kx(a, l, r) * kx(b, m, c), 2);
+        }
     }
+    return S;
+}
+
+// coefficients for this res, rounded as the single-precision products res, res * res
+TermTable term_table(float res) {
+    static const TermShape S = make_term_shape();
+    TermTable T{};
+    const float p[3] = {1.f, res, res * res};
+    for (int e = 0; e < 21; ++e)
+        for (int u = 0; u < 9; ++u) {
+            T.idx[e][u] = S.idx[e][u];
+            T.coef[e][u] = S.sgn[e][u] == 0 ? 0.f : (S.sgn[e][u] > 0 ? p[S.pw[e][u]] : -p[S.pw[e][u]]);
+        }
+    return T;
 }
 
 // NG gather warps, NM metric warps (NG a multiple of NM), NS pose stages per gather warp,
 // L2 prefetch NP poses beyond the stages
 template <int kElem, int NG, int NM, int NS, int NP>
-__global__ void __launch_bounds__((NG + NM) * 32, 1) query_kernel(QueryArgs args) {
+__global__ void __launch_bounds__((NG + NM) * 32, 1) query_kernel(QueryArgs args, TermTable tt) {
     using L = Layout<kElem>;
     using GS = GatherSmem<kElem, NS>;
     constexpr int kStages = NS;
@@ -178,8 +211,12 @@ __global__ void __launch_bounds__((NG + NM) * 32, 1) query_kernel(QueryArgs args
         const int corner_off = L::slot(j >> 1) + bx * L::kNodeBytes;
         int t_idx[9];
         float t_coef[9];
+        const int te = lane < 21 ? lane : 0;
 #pragma unroll
-        for (int u = 0; u < 9; ++u) t_term(lane < 21 ? lane : 0, args.res, u, t_idx[u], t_coef[u]);
+        for (int u = 0; u < 9; ++u) {
+            t_idx[u] = tt.idx[te][u];
+            t_coef[u] = tt.coef[te][u];
+        }
         const int64_t nx = args.nx, nxy = (int64_t)args.nx * args.ny;
         const char* coeffs = reinterpret_cast<const char*>(args.coeffs);
         auto pair_src = [&](int64_t base, int pp) -> const void* {
@@ -475,7 +512,7 @@ int launch_query_cfg(const QueryArgs& a, cudaStream_t stream) {
     const int64_t need = (groups + NG - 1) / NG;
     const int64_t grid = std::min<int64_t>(need, (int64_t)sms);
     if (grid <= 0) return FIF_OK;
-    kern<<<(unsigned)grid, (NG + NM) * 32, smem, stream>>>(a);
+    kern<<<(unsigned)grid, (NG + NM) * 32, smem, stream>>>(a, term_table(a.res));
     return cudaPeekAtLastError() == cudaSuccess ? FIF_OK : FIF_ECUDA;
 }
 

@@ -87,6 +87,9 @@ _SIGS = {
     "fif_build_static": (_I32, [ctypes.POINTER(FieldC), _VP, _I64, _VP]),
     "fif_build_update": (_I32, [ctypes.POINTER(FieldC), _VP, _I64, _I32, _VP, ctypes.c_size_t, _VP]),
     "fif_query": (_I32, [ctypes.POINTER(FieldC), _VP, _I64, _I32, _VP, _VP, _VP, _VP, _VP]),
+    "fif_query_host_staging_bytes": (ctypes.c_size_t, [_I64]),
+    "fif_query_host": (_I32, [ctypes.POINTER(FieldC), _VP, _I64, _I32, _VP, _VP, _VP, _VP, _I64, _VP,
+                              ctypes.c_size_t, _VP, _VP]),
     "fif_query_backward": (_I32, [ctypes.POINTER(FieldC), _VP, _I64, _I32, _VP, _VP, _VP, _VP]),
     "fif_pointcloud_fim": (_I32, [_VP, _I64, ctypes.POINTER(Params), ctypes.POINTER(Pinhole), _VP, _I64, _I32,
                                   _VP, _VP, _VP, _VP, _VP]),
@@ -352,6 +355,25 @@ def query(field: FieldC, poses: torch.Tensor, flags=Q_METRICS, fim=None, metrics
     assert poses.is_cuda and poses.dtype == torch.float32 and poses.is_contiguous()
     _check(lib().fif_query(ctypes.byref(field), _ptr(poses), poses.shape[0], int(flags), _ptr(fim), _ptr(metrics),
                            _ptr(sign), _ptr(status), _stream(stream)), "fif_query")
+
+
+def query_host_staging_bytes(chunk: int) -> int:
+    return int(lib().fif_query_host_staging_bytes(int(chunk)))
+
+
+def query_host(field: FieldC, poses: torch.Tensor, flags=Q_METRICS, fim=None, metrics=None, sign=None, status=None,
+               chunk=1 << 18, staging=None, stream=None, copy_stream=None):
+    """fif_query_host: poses and outputs are CPU tensors (pinned for overlapped copies); staging is
+    a device uint8 tensor of at least query_host_staging_bytes(chunk) bytes; copy_stream a
+    torch.cuda.Stream other than stream."""
+    assert not poses.is_cuda and poses.dtype == torch.float32 and poses.is_contiguous()
+    for t in (fim, metrics, sign, status):
+        assert t is None or (not t.is_cuda and t.is_contiguous())
+    assert staging is not None and staging.is_cuda and copy_stream is not None
+    _check(lib().fif_query_host(ctypes.byref(field), _ptr(poses), poses.shape[0], int(flags), _ptr(fim), _ptr(metrics),
+                                _ptr(sign), _ptr(status), int(chunk), _ptr(staging),
+                                staging.numel() * staging.element_size(), _stream(stream), _stream(copy_stream)),
+           "fif_query_host")
 
 
 def query_backward(field: FieldC, poses, fim, grad_metrics, grad_pose, flags=Q_METRICS, stream=None):

@@ -105,3 +105,29 @@ def test_calls_reject_bad_arguments_before_any_launch(F):
     assert lib.fif_field_load(None, b"/nonexistent", fake, 16, None, None) == F.EINVAL
     f2 = F.FieldC()
     assert lib.fif_field_load(ctypes.byref(f2), b"/nonexistent/x.fif", fake, 16, None, None) == F.EIO
+
+
+def test_query_host_checks_and_staging_size(F):
+    """fif_query_host's argument checks return before any CUDA call; its staging is two buffers of
+    poses + FIM + metrics + sign + status per pose, each array rounded up to 256 bytes."""
+    up = lambda x: (x + 255) // 256 * 256
+    assert F.query_host_staging_bytes(1000) == 2 * (up(28000) + up(84000) + up(24000) + up(1000) + up(4000))
+    assert F.query_host_staging_bytes(0) == 0 and F.query_host_staging_bytes(-3) == 0
+    lib = F.lib()
+    g = F.make_grid((0, 0, 0), 0.5, (4, 4, 4))
+    p = F.make_params()
+    f = F.FieldC()
+    fake = ctypes.c_void_p(0x100000)
+    s1, s2 = ctypes.c_void_p(0x10), ctypes.c_void_p(0x20)   # never used: every call below fails its checks
+    assert lib.fif_field_init(ctypes.byref(f), ctypes.byref(g), ctypes.byref(p), 0, fake, F.field_bytes(g, 0)) == 0
+    need = F.query_host_staging_bytes(64)
+    q = lib.fif_query_host
+    assert q(ctypes.byref(f), fake, -1, F.Q_METRICS, None, fake, None, None, 64, fake, need, s1, s2) == F.EINVAL
+    assert q(ctypes.byref(f), None, 5, F.Q_METRICS, None, fake, None, None, 64, fake, need, s1, s2) == F.EINVAL
+    assert q(ctypes.byref(f), fake, 0, F.Q_METRICS, None, fake, None, None, 64, fake, need, s1, s2) == F.OK
+    assert q(ctypes.byref(f), fake, 5, F.Q_METRICS, None, fake, None, None, 0, fake, need, s1, s2) == F.EINVAL
+    assert q(ctypes.byref(f), fake, 5, F.Q_METRICS, None, fake, None, None, 64, None, need, s1, s2) == F.EINVAL
+    assert q(ctypes.byref(f), fake, 5, F.Q_METRICS, None, fake, None, None, 64, fake, need, s1, s1) == F.EINVAL
+    assert q(ctypes.byref(f), fake, 5, F.Q_METRICS, None, fake, None, None, 64, fake, need - 1, s1, s2) == F.ESIZE
+    assert q(ctypes.byref(f), fake, 5, F.Q_METRICS, None, fake, None, None, 64, ctypes.c_void_p(0x100004), need,
+             s1, s2) == F.EALIGN

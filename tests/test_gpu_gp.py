@@ -152,6 +152,33 @@ def test_gp_build_room_all_nodes(F, ns):
     assert F.build_stats(ws, field, len(sc.landmarks))[0] == pairs
 
 
+@pytest.mark.parametrize("ns", [12, 40, 65])
+def test_gp_build_last_slot_packing(F, ns):
+    """Sample counts whose last slot of 32 axes holds r <= 16 samples, so that slot takes
+    32 // r landmarks per pass (12: two per pass in the only slot; 40: r = 8, four per pass;
+    65: r = 1, 32 per pass): every node of the room against the oracle, pads zero, and the
+    in-shell pair count exact.  The stored basis does not depend on the length scale."""
+    sc = X.room_scene()
+    spec = X.ROOM["grid"]
+    axes = synth.fibonacci_sphere(ns)
+    field = F.Field(spec.origin, spec.res, spec.dims, room_params(F), storage=F.STORAGE_GP, gp=F.GPModel(axes, 0.7))
+    ws = field.build(torch.from_numpy(sc.landmarks).cuda())
+    torch.cuda.synchronize()
+    assert F.device_error() == 0
+    rs, stride = F.gp_row_stride(ns), F.gp_stride(ns)
+    buf = field.coeffs.cpu().numpy()
+    ref = O.field_nodes_gp(sc.landmarks, X.oracle_grid(spec), room_params(), O.GP(axes, 0.7), np.arange(spec.n_nodes),
+                           about_node=True, basis="sigmoid")
+    err = node_rel_err(unpack_gp(buf, ns, rs), ref)
+    assert err.max() <= X.TAU_F32, err.max()
+    mask = np.ones(stride, bool)
+    for e in range(21):
+        mask[e * rs:e * rs + ns] = False
+    assert np.all(buf[:, mask] == 0)
+    pairs = O.field_pairs(sc.landmarks, X.oracle_grid(spec), room_params(), np.arange(spec.n_nodes))
+    assert F.build_stats(ws, field, len(sc.landmarks))[0] == pairs
+
+
 def test_gp_build_warehouse_sampled_nodes(F):
     ns = 30
     sc = X.warehouse_scene()

@@ -182,3 +182,45 @@ def test_metrics_of_the_returned_fim(F, storage):
     np.testing.assert_array_equal(sg[ok], mo[ok, 2].astype(np.int8))
     assert np.all(np.abs(met[:, 2] - mo[:, 3]) <= 1e-7 * n)
     assert np.all(np.abs(met[:, 0] - np.trace(I, axis1=1, axis2=2)) <= 1e-6 * n)
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_query_host_matches_device(F, storage):
+    """fif_query_host (pinned host buffers, chunks double-buffered through device staging, copies
+    on a second stream) gives every pose exactly the results fif_query gives it on the device:
+    a ragged last chunk, a chunk larger than the batch, a subset of the outputs, the empty
+    batch and the argument checks."""
+    field = uploaded_room_field(F, storage=storage)
+    poses = X.room_poses(3000)[:2517]
+    fim, met, sg, st = run(F, field, poses)
+    h_poses = torch.from_numpy(np.ascontiguousarray(poses, np.float32)).pin_memory()
+    cs = torch.cuda.Stream()
+    for chunk in (700, 4096):
+        staging = torch.empty(F.query_host_staging_bytes(chunk), dtype=torch.uint8, device="cuda")
+        h_fim = torch.full((len(poses), 21), np.nan, dtype=torch.float32).pin_memory()
+        h_met = torch.full((len(poses), 3), np.nan, dtype=torch.float64).pin_memory()
+        h_sg = torch.zeros(len(poses), dtype=torch.int8).pin_memory()
+        h_st = torch.full((len(poses),), -1, dtype=torch.int32).pin_memory()
+        F.query_host(field.c, h_poses, F.Q_METRICS, h_fim, h_met, h_sg, h_st, chunk=chunk, staging=staging,
+                     copy_stream=cs)
+        torch.cuda.current_stream().synchronize()
+        assert F.device_error() == 0
+        np.testing.assert_array_equal(h_fim.numpy(), fim)
+        np.testing.assert_array_equal(h_met.numpy(), met)
+        np.testing.assert_array_equal(h_sg.numpy(), sg)
+        np.testing.assert_array_equal(h_st.numpy(), st)
+    # metrics only (no FIM buffer), chunk of 512
+    staging = torch.empty(F.query_host_staging_bytes(512), dtype=torch.uint8, device="cuda")
+    h_met = torch.full((len(poses), 3), np.nan, dtype=torch.float64).pin_memory()
+    F.query_host(field.c, h_poses, F.Q_METRICS, None, h_met, None, None, chunk=512, staging=staging, copy_stream=cs)
+    torch.cuda.current_stream().synchronize()
+    np.testing.assert_array_equal(h_met.numpy(), met)
+    # empty batch, undersized staging, the same stream twice
+    F.query_host(field.c, h_poses[:0], F.Q_METRICS, None, h_met[:0], None, None, chunk=512, staging=staging,
+                 copy_stream=cs)
+    with pytest.raises(F.FifError):
+        F.query_host(field.c, h_poses, F.Q_METRICS, None, h_met, None, None, chunk=4096, staging=staging,
+                     copy_stream=cs)
+    with pytest.raises(F.FifError):
+        F.query_host(field.c, h_poses, F.Q_METRICS, None, h_met, None, None, chunk=512, staging=staging,
+                     copy_stream=torch.cuda.current_stream())
