@@ -22,8 +22,9 @@
 // of 66 moments
 //   sum u^a / n^2 (|a| = 4, 3),  sum u^a / n (|a| = 3, 2),  sum u^a (|a| = 4, 3),
 // and the hot loop accumulates only those 66 (31 monomials + 66 FMA/FADD per pair).
-// Accumulation is compensated: a block of up to 64 pairs is summed in registers, then the
-// block sum is added to a Kahan (sum, compensation) pair held in shared memory.  The
+// Accumulation is compensated: a block of 64 pairs (carried across tiles) is summed in
+// registers, then the block sum is added to a Kahan (sum, compensation) pair held in shared
+// memory.  The
 // epilogue expands the 66 moments into the 210 stored coefficients.
 #include "fif_common.cuh"
 #include "fif_internal.h"
@@ -299,6 +300,26 @@ __global__ void __launch_bounds__(kThreads, 2) build_kernel(BuildArgs a) {
     zero_block();
     float* hs = &S.hi[0][0];
     float* ls = &S.lo[0][0];
+    // compensated merge of the register block into the shared Kahan pairs (moment order)
+    auto merge_block = [&]() {
+        auto merge2 = [&](int base, const float2* v, int npairs) {
+#pragma unroll
+            for (int i = 0; i < npairs; ++i) {
+                kahan_merge(hs, ls, (base + 2 * i) * kThreads + tid, v[i].x);
+                kahan_merge(hs, ls, (base + 2 * i + 1) * kThreads + tid, v[i].y);
+            }
+        };
+        merge2(kS4n2, a4n2, 7);
+        kahan_merge(hs, ls, (kS4n2 + 14) * kThreads + tid, a4n2_14);
+        merge2(kS3n2, a3n2, 5);
+        merge2(kS3n1, a3n1, 5);
+        merge2(kS2n1, a2n1, 3);
+        merge2(kS4n0, a4n0, 7);
+        kahan_merge(hs, ls, (kS4n0 + 14) * kThreads + tid, a4n0_14);
+        merge2(kS3n0, a3n0, 5);
+        zero_block();
+    };
+    int blk = 0;   // pairs in the register block (warp-uniform); the block spans tiles
     unsigned int in_pairs = 0;
     unsigned long long cand = 0;
     bool ok = true;
@@ -332,9 +353,10 @@ __global__ void __launch_bounds__(kThreads, 2) build_kernel(BuildArgs a) {
         }
         __syncwarp();
         cand += nkeep;
-        for (int b0 = 0; b0 < nkeep; b0 += kBlock) {
-            const int b1 = min(nkeep, b0 + kBlock);
-#pragma unroll 2
+        for (int b0 = 0; b0 < nkeep;) {
+            const int b1 = min(nkeep, b0 + (kBlock - blk));
+            blk += b1 - b0;
+#pragma unroll 4
             for (int l = b0; l < b1; ++l) {
                 const float4 L = tile[keep[l]];
                 const float dx = __fsub_rn(L.x, cx), dy = __fsub_rn(L.y, cy), dz = __fsub_rn(L.z, cz);
@@ -386,23 +408,11 @@ __global__ void __launch_bounds__(kThreads, 2) build_kernel(BuildArgs a) {
 #pragma unroll
                 for (int i = 0; i < 5; ++i) a3n0[i] = add2(a3n0[i], m3[i]);
             }
-            // compensated merge of the block sums (moment order)
-            auto merge2 = [&](int base, const float2* v, int npairs) {
-#pragma unroll
-                for (int i = 0; i < npairs; ++i) {
-                    kahan_merge(hs, ls, (base + 2 * i) * kThreads + tid, v[i].x);
-                    kahan_merge(hs, ls, (base + 2 * i + 1) * kThreads + tid, v[i].y);
-                }
-            };
-            merge2(kS4n2, a4n2, 7);
-            kahan_merge(hs, ls, (kS4n2 + 14) * kThreads + tid, a4n2_14);
-            merge2(kS3n2, a3n2, 5);
-            merge2(kS3n1, a3n1, 5);
-            merge2(kS2n1, a2n1, 3);
-            merge2(kS4n0, a4n0, 7);
-            kahan_merge(hs, ls, (kS4n0 + 14) * kThreads + tid, a4n0_14);
-            merge2(kS3n0, a3n0, 5);
-            zero_block();
+            b0 = b1;
+            if (blk == kBlock) {
+                merge_block();
+                blk = 0;
+            }
         }
         __syncthreads();  // everyone is done with this slot
         if (tid == 0) {
@@ -410,6 +420,7 @@ __global__ void __launch_bounds__(kThreads, 2) build_kernel(BuildArgs a) {
             produce(slot);
         }
     }
+    if (blk > 0) merge_block();
     // statistics
     {
         unsigned long long* stats = reinterpret_cast<unsigned long long*>(a.ws + a.lay.stats);
