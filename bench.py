@@ -44,17 +44,17 @@ WORKLOAD = ("warehouse 50x50x10 m, 200k landmarks (60% box faces / 40% walls, 40
 QUERY_BYTES_PER_POSE = 8 * 210 * 4 + 7 * 4 + 21 * 4 + 3 * 8 + 1 + 4   # corners + pose + outputs
 BUILD_FLOPS_PER_PAIR = 151   # shell test 8, rsqrt 1, bearing 4, monomials 31, 66 accumulations 107
 # DRAM traffic of one query launch per pose, from the ncu capture summarised in
-# profiles/query_kernel_warehouse_4M.md (read 29.018 GB + write 0.476 GB for 4,194,304 poses),
+# profiles/query_kernel_warehouse_4M.md (read 29.015 GB + write 0.475 GB for 4,194,304 poses),
 # valid while the kernel sources hash to the recorded digest
-QUERY_TRAFFIC = {"bytes_per_pose": (29.017812e9 + 0.475997e9) / 4194304,
-                 "digest": "e7fad0a4b4702022"}
+QUERY_TRAFFIC = {"bytes_per_pose": (29.014592e9 + 0.474674e9) / 4194304,
+                 "digest": "7307f54a5e67b276"}
 # the same for the GP query (N_s = 70) from profiles/gp_query_kernel_warehouse_nz8.md
 # (read 11.723 GB + write 0.0116 GB for 262,144 poses on the 200 x 200 x 8 lattice)
 GP_QUERY_TRAFFIC = {"bytes_per_pose": (11.722718e9 + 0.011555e9) / 262144, "n_samples": 70,
                     "digest": "72d025933a00cc55"}
 # FMA-pipe utilisation of build_kernel (ncu sm__pipe_fma_cycles_active, profiles/build_kernel_warehouse_nz8.md),
 # valid while the build sources hash to the recorded digest
-BUILD_PIPE = {"fma_pipe_active": 0.643, "digest": "47fe25de634907bf"}
+BUILD_PIPE = {"fma_pipe_active": 0.656, "digest": "05668e59f8af29ff"}
 # GP build, per (in-shell pair, sample axis): sigmoid 10 (dot 6, shift 1, exp 1, add 1, rcp 1)
 # + 15 moment accumulations 30; per pair: bearing products 16
 GP_FLOPS_PER_PAIR_SAMPLE = 40
