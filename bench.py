@@ -160,6 +160,20 @@ def time_events(fn, steps, warmup, stream):
     return [a.elapsed_time(b) for a, b in evs]
 
 
+def fma_probe_tflops(fif, dev, stream, blocks=8 * 152, iters=1 << 14):
+    """Measured FP32 FMA throughput of this GPU (fif_fma_probe: eight independent chains per
+    thread, scalar or packed f32x2), best of five launches: context for the nominal peak the
+    ALU-bound build is reported against."""
+    import torch
+    sink = torch.empty(blocks * 256, dtype=torch.float32, device=dev)
+    out = {}
+    for name, packed in (("scalar", False), ("packed_f32x2", True)):
+        t = time_events(lambda: fif.fma_probe(sink, blocks, iters, packed, stream), 5, 2, stream)
+        out[name] = 2 * 8 * iters * blocks * 256 / (min(t) * 1e-3) / 1e12
+    assert bool(torch.isfinite(sink).all())
+    return out
+
+
 def cpu_baseline(scene, spec, r_max, seed=123, n_poses=256, min_query_s=2.0):
     """The FP64 oracle on a bounded sample of the same workload, on the host cores:
     build the corner nodes of `n_poses` random poses (timed: pairs/s), then query them
@@ -418,7 +432,8 @@ def main():
                      "peak_kind": "nominal FP32: 152 SMs x 128 lanes x 2 x 2070 MHz",
                      "fma_pipe_active_ncu": (BUILD_PIPE["fma_pipe_active"] if BUILD_PIPE["digest"] ==
                                              query_source_digest(("build.cu", "landmark_stream.cuh", "fif_common.cuh"))
-                                             else None)},
+                                             else None),
+                     "fma_probe_tflops": fma_probe_tflops(fif, dev, stream)},
     }
     assert fif.device_error() == 0
     if args.phase == "build":

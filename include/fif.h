@@ -389,6 +389,13 @@ FIF_API int32_t fif_field_load(fif_field* field, const char* path, void* d_coeff
  * 0 when no bounded device wait has run out since the last reset.  Synchronises `stream`. */
 FIF_API int32_t fif_device_error(int32_t* out_code, int32_t reset, fif_stream_t stream);
 
+/* FP32 FMA throughput probe (measurement infrastructure for the roofline of the ALU-bound
+ * builds, not part of the method): `blocks` CTAs of 256 threads each run `iters` rounds of
+ * eight independent single-precision FMA chains (packed != 0: four chains of packed f32x2 FMAs,
+ * the same eight lanes of work), 2 * 8 * iters flops per thread, and write one float per thread
+ * to d_sink (device, at least blocks * 256 floats).  Time it with events on `stream`. */
+FIF_API int32_t fif_fma_probe(float* d_sink, int64_t blocks, int32_t iters, int32_t packed, fif_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

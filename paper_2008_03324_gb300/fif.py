@@ -87,6 +87,7 @@ _SIGS = {
     "fif_build_static": (_I32, [ctypes.POINTER(FieldC), _VP, _I64, _VP]),
     "fif_build_update": (_I32, [ctypes.POINTER(FieldC), _VP, _I64, _I32, _VP, ctypes.c_size_t, _VP]),
     "fif_query": (_I32, [ctypes.POINTER(FieldC), _VP, _I64, _I32, _VP, _VP, _VP, _VP, _VP]),
+    "fif_fma_probe": (_I32, [_VP, _I64, _I32, _I32, _VP]),
     "fif_query_host_staging_bytes": (ctypes.c_size_t, [_I64]),
     "fif_query_host": (_I32, [ctypes.POINTER(FieldC), _VP, _I64, _I32, _VP, _VP, _VP, _VP, _I64, _VP,
                               ctypes.c_size_t, _VP, _VP]),
@@ -355,6 +356,14 @@ def query(field: FieldC, poses: torch.Tensor, flags=Q_METRICS, fim=None, metrics
     assert poses.is_cuda and poses.dtype == torch.float32 and poses.is_contiguous()
     _check(lib().fif_query(ctypes.byref(field), _ptr(poses), poses.shape[0], int(flags), _ptr(fim), _ptr(metrics),
                            _ptr(sign), _ptr(status), _stream(stream)), "fif_query")
+
+
+def fma_probe(sink: torch.Tensor, blocks: int, iters: int, packed: bool, stream=None):
+    """fif_fma_probe: FP32 FMA throughput probe (2 * 8 * iters flops per thread, 256 threads per
+    block); sink is a float32 device tensor of at least blocks * 256 elements."""
+    assert sink.is_cuda and sink.dtype == torch.float32 and sink.numel() >= blocks * 256
+    _check(lib().fif_fma_probe(_ptr(sink), int(blocks), int(iters), int(bool(packed)), _stream(stream)),
+           "fif_fma_probe")
 
 
 def query_host_staging_bytes(chunk: int) -> int:

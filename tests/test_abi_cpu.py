@@ -102,6 +102,10 @@ def test_calls_reject_bad_arguments_before_any_launch(F):
     assert lib.fif_pointcloud_fim(fake, 5, ctypes.byref(p), ctypes.byref(cam), fake, 5, F.Q_METRICS,
                                   None, fake, None, None, None) == F.EINVAL
     assert lib.fif_device_error(None, 0, None) == F.EINVAL
+    assert lib.fif_fma_probe(None, 4, 10, 0, None) == F.EINVAL
+    assert lib.fif_fma_probe(fake, 0, 10, 0, None) == F.EINVAL
+    assert lib.fif_fma_probe(fake, 4, 0, 1, None) == F.EINVAL
+    assert lib.fif_fma_probe(ctypes.c_void_p(0x100002), 4, 10, 0, None) == F.EALIGN
     assert lib.fif_field_load(None, b"/nonexistent", fake, 16, None, None) == F.EINVAL
     f2 = F.FieldC()
     assert lib.fif_field_load(ctypes.byref(f2), b"/nonexistent/x.fif", fake, 16, None, None) == F.EIO

@@ -224,3 +224,15 @@ def test_query_host_matches_device(F, storage):
     with pytest.raises(F.FifError):
         F.query_host(field.c, h_poses, F.Q_METRICS, None, h_met, None, None, chunk=512, staging=staging,
                      copy_stream=torch.cuda.current_stream())
+
+
+def test_fma_probe_runs(F):
+    """The FP32 FMA throughput probe (measurement infrastructure) runs in both forms and leaves
+    finite values; bad arguments are rejected."""
+    sink = torch.full((4 * 256,), float("nan"), device="cuda")
+    for packed in (False, True):
+        F.fma_probe(sink, 4, 1000, packed)
+        torch.cuda.synchronize()
+        assert bool(torch.isfinite(sink).all())
+    assert F.lib().fif_fma_probe(None, 4, 10, 0, None) == F.EINVAL
+    assert F.lib().fif_fma_probe(sink.data_ptr(), 4, 0, 0, None) == F.EINVAL
