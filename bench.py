@@ -435,6 +435,17 @@ def main():
                                              else None),
                      "fma_probe_tflops": fma_probe_tflops(fif, dev, stream)},
     }
+    # ---------------- incremental update (Sec. VI-A-1): add then remove 1,000 landmarks ----------------
+    delta = torch.from_numpy(synth.random_box(seed=21, n=1000, size=(50.0, 50.0, 10.0))).to(dev)
+    wsu = torch.empty(fif.build_workspace_bytes(field.c, delta.shape[0]), dtype=torch.uint8, device=dev)
+    tu = time_events(lambda: (fif.build_update(field.c, delta, +1, wsu), fif.build_update(field.c, delta, -1, wsu)),
+                     3, 1, stream)
+    u_pairs = fif.build_stats(wsu, field, delta.shape[0])[0]
+    u_ms = float(np.mean(tu)) / 2
+    out["build"]["update"] = {"landmarks": int(delta.shape[0]), "ms_per_update": u_ms,
+                              "in_shell_pairs": int(u_pairs), "pairs_per_s": u_pairs / (u_ms * 1e-3),
+                              "note": "add then remove the same 1,000 random landmarks; only nodes within r_max change"}
+    del wsu
     assert fif.device_error() == 0
     if args.phase == "build":
         if rank == 0:
