@@ -32,6 +32,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <utility>
 
 namespace fif {
 
@@ -46,14 +47,14 @@ constexpr int kMaxRuns = 2048;
 constexpr int kMom = 66;
 
 // monomial exponent tables (order fixed by the hot loop)
-__device__ __constant__ int8_t kMon2[6][3] = {{2, 0, 0}, {0, 2, 0}, {0, 0, 2}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1}};
-__device__ __constant__ int8_t kMon3[10][3] = {{3, 0, 0}, {0, 3, 0}, {0, 0, 3}, {2, 1, 0}, {2, 0, 1},
+constexpr int8_t kMon2[6][3] = {{2, 0, 0}, {0, 2, 0}, {0, 0, 2}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1}};
+constexpr int8_t kMon3[10][3] = {{3, 0, 0}, {0, 3, 0}, {0, 0, 3}, {2, 1, 0}, {2, 0, 1},
                                                {1, 2, 0}, {0, 2, 1}, {1, 0, 2}, {0, 1, 2}, {1, 1, 1}};
-__device__ __constant__ int8_t kMon4[15][3] = {{4, 0, 0}, {0, 4, 0}, {0, 0, 4}, {3, 1, 0}, {3, 0, 1},
+constexpr int8_t kMon4[15][3] = {{4, 0, 0}, {0, 4, 0}, {0, 0, 4}, {3, 1, 0}, {3, 0, 1},
                                                {1, 3, 0}, {0, 3, 1}, {1, 0, 3}, {0, 1, 3}, {2, 2, 0},
                                                {2, 0, 2}, {0, 2, 2}, {2, 1, 1}, {1, 2, 1}, {1, 1, 2}};
 // v_p monomials of Eq. quad_vis_component
-__device__ __constant__ int8_t kVp[10][3] = {{2, 0, 0}, {0, 2, 0}, {0, 0, 2}, {1, 1, 0}, {1, 0, 1},
+constexpr int8_t kVp[10][3] = {{2, 0, 0}, {0, 2, 0}, {0, 0, 2}, {1, 1, 0}, {1, 0, 1},
                                              {0, 1, 1}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {0, 0, 0}};
 // moment blocks: base index of (power of 1/n, degree)
 constexpr int kS4n2 = 0, kS3n2 = 15, kS3n1 = 25, kS2n1 = 35, kS4n0 = 41, kS3n0 = 56;
@@ -165,61 +166,175 @@ struct BuildSmem {
     uint64_t bars[kSlots];
 };
 
-// sum u^a / n^p for a stored degree (|a| = 4 or 3 for p = 0, 2; 3 or 2 for p = 1)
-__device__ float moment_direct(const float* hs, const float* ls, int tid, int p, int ex, int ey, int ez) {
+// ---- moments -> coefficients -----------------------------------------------------------
+// Entry e (upper-triangular 6x6) of the node-local C_k is a fixed integer combination of the 66
+// moments (before 1/sigma^2):
+//   TT: (delta_rc - u_r u_c)/n^2,  TR: (-[u]x)_{r b}/n = eps_{r b l} u_l / n,  RR: delta_ab - u_a u_b,
+// each times the monomial v_p[k](u), with monomials below the stored degrees raised by u.u = 1
+// (one or two levels).  The combination is enumerated at compile time, so the epilogue is a
+// short sum of register moments per coefficient.
+struct CoefTerm {
+    int8_t idx, w;   // moment index, integer weight
+};
+struct CoefRow {
+    CoefTerm t[12];
+    int n;
+};
+struct CoefTable {
+    CoefRow row[210];   // o = 21 k + e
+};
+
+constexpr void add_stored(CoefRow& r, int p, int ex, int ey, int ez, int w) {
     const int deg = ex + ey + ez;
-    int base, cnt;
-    const int8_t(*tab)[3];
-    if (deg == 4) { tab = kMon4; cnt = 15; base = (p == 2) ? kS4n2 : kS4n0; }
-    else if (deg == 3) { tab = kMon3; cnt = 10; base = (p == 2) ? kS3n2 : (p == 1) ? kS3n1 : kS3n0; }
-    else { tab = kMon2; cnt = 6; base = kS2n1; }
-    for (int i = 0; i < cnt; ++i)
-        if (tab[i][0] == ex && tab[i][1] == ey && tab[i][2] == ez) {
-            const int idx = base + i;
-            return hs[idx * kThreads + tid] - ls[idx * kThreads + tid];
+    int base = kS2n1, cnt = 6, idx = -1;
+    if (deg == 4) { base = (p == 2) ? kS4n2 : kS4n0; cnt = 15; }
+    else if (deg == 3) { base = (p == 2) ? kS3n2 : (p == 1) ? kS3n1 : kS3n0; cnt = 10; }
+    for (int i = 0; i < cnt; ++i) {
+        const int8_t* m = deg == 4 ? kMon4[i] : deg == 3 ? kMon3[i] : kMon2[i];
+        if (m[0] == ex && m[1] == ey && m[2] == ez) idx = base + i;
+    }
+    for (int i = 0; i < r.n; ++i)
+        if (r.t[i].idx == idx) {
+            r.t[i].w = (int8_t)(r.t[i].w + w);
+            return;
         }
-    return 0.f;
+    r.t[r.n].idx = (int8_t)idx;
+    r.t[r.n].w = (int8_t)w;
+    ++r.n;
 }
 
-// sum u^a / n^p for any |a| <= 4: lower degrees are raised with u.u = 1 (one or two levels)
-__device__ float moment(const float* hs, const float* ls, int tid, int p, int ex, int ey, int ez) {
+// w * sum u^a / n^p for any |a| <= 4 (stored degrees: 4 and 3 for p = 0, 2; 3 and 2 for p = 1)
+constexpr void add_moment(CoefRow& r, int p, int ex, int ey, int ez, int w) {
     const int top = (p == 1) ? 3 : 4;
-    if (ex + ey + ez >= top - 1) return moment_direct(hs, ls, tid, p, ex, ey, ez);
-    float s = 0.f;
+    if (ex + ey + ez >= top - 1) {
+        add_stored(r, p, ex, ey, ez, w);
+        return;
+    }
     for (int c = 0; c < 3; ++c) {
         const int a0 = ex + (c == 0 ? 2 : 0), a1 = ey + (c == 1 ? 2 : 0), a2 = ez + (c == 2 ? 2 : 0);
         if (a0 + a1 + a2 >= top - 1) {
-            s += moment_direct(hs, ls, tid, p, a0, a1, a2);
+            add_stored(r, p, a0, a1, a2, w);
         } else {
             for (int d = 0; d < 3; ++d)
-                s += moment_direct(hs, ls, tid, p, a0 + (d == 0 ? 2 : 0), a1 + (d == 1 ? 2 : 0), a2 + (d == 2 ? 2 : 0));
+                add_stored(r, p, a0 + (d == 0 ? 2 : 0), a1 + (d == 1 ? 2 : 0), a2 + (d == 2 ? 2 : 0), w);
         }
     }
-    return s;
 }
 
-// entry e (upper-triangular 6x6) of the node-local C_k, from the moments (before 1/sigma^2):
-//   TT: (delta_rc - u_r u_c)/n^2,  TR: (-[u]x)_{r b}/n = eps_{r b l} u_l / n,  RR: delta_ab - u_a u_b,
-// each times the monomial v_p[k](u)
-__device__ float coef_local(const float* hs, const float* ls, int tid, int k, int e) {
-    const int r = sym_row(e), c = sym_col(e);
-    const int mx = kVp[k][0], my = kVp[k][1], mz = kVp[k][2];
-    if (r < 3 && c < 3) {
-        float v = -moment(hs, ls, tid, 2, mx + (r == 0) + (c == 0), my + (r == 1) + (c == 1), mz + (r == 2) + (c == 2));
-        if (r == c) v += moment(hs, ls, tid, 2, mx, my, mz);
+constexpr CoefTable make_coef_table() {
+    CoefTable T{};
+    for (int k = 0; k < 10; ++k)
+        for (int e = 0; e < 21; ++e) {
+            CoefRow& row = T.row[21 * k + e];
+            const int r = sym_row(e), c = sym_col(e);
+            const int mx = kVp[k][0], my = kVp[k][1], mz = kVp[k][2];
+            if (r < 3 && c < 3) {
+                add_moment(row, 2, mx + (r == 0) + (c == 0), my + (r == 1) + (c == 1), mz + (r == 2) + (c == 2), -1);
+                if (r == c) add_moment(row, 2, mx, my, mz, 1);
+            } else if (r < 3) {
+                const int b = c - 3;
+                if (r != b) {
+                    const int l = 3 - r - b;
+                    add_moment(row, 1, mx + (l == 0), my + (l == 1), mz + (l == 2), ((r + 1) % 3 == b) ? 1 : -1);
+                }
+            } else {
+                const int ra = r - 3, cb = c - 3;
+                add_moment(row, 0, mx + (ra == 0) + (cb == 0), my + (ra == 1) + (cb == 1), mz + (ra == 2) + (cb == 2), -1);
+                if (ra == cb) add_moment(row, 0, mx, my, mz, 1);
+            }
+            // drop cancelled terms
+            int n = 0;
+            for (int i = 0; i < row.n; ++i)
+                if (row.t[i].w != 0) row.t[n++] = row.t[i];
+            row.n = n;
+        }
+    return T;
+}
+
+constexpr CoefTable kCoefTable = make_coef_table();
+
+// coefficient o (o >= 210: a zero pad) from the node's moments
+template <int O>
+FIF_DEV float coef_of(const float (&m)[kMom]) {
+    if constexpr (O >= 210) {
+        return 0.f;
+    } else {
+        constexpr CoefRow R = kCoefTable.row[O];
+        float v = 0.f;
+#pragma unroll
+        for (int t = 0; t < R.n; ++t) v = fmaf((float)R.t[t].w, m[R.t[t].idx], v);
         return v;
     }
-    if (r < 3) {
-        const int b = c - 3;
-        if (r == b) return 0.f;
-        const int l = 3 - r - b;
-        const float sgn = ((r + 1) % 3 == b) ? 1.f : -1.f;  // eps_{r b l}
-        return sgn * moment(hs, ls, tid, 1, mx + (l == 0), my + (l == 1), mz + (l == 2));
+}
+
+// float32 storage: float4 group G of the node record (stride 216 = 54 groups)
+template <int... G>
+FIF_DEV void store_f32(float4* dst, const float (&m)[kMom], float scale, int acc, std::integer_sequence<int, G...>) {
+    auto one = [&](float4* d, float4 v) {
+        if (acc != 0) {
+            const float sgn = (float)acc;
+            const float4 old = *d;
+            v = make_float4(fmaf(sgn, v.x, old.x), fmaf(sgn, v.y, old.y), fmaf(sgn, v.z, old.z), fmaf(sgn, v.w, old.w));
+        }
+        *d = v;
+    };
+    (one(dst + G, make_float4(coef_of<4 * G>(m) * scale, coef_of<4 * G + 1>(m) * scale, coef_of<4 * G + 2>(m) * scale,
+                              coef_of<4 * G + 3>(m) * scale)),
+     ...);
+}
+
+// bfloat16 storage: element O of the node record (stride 224)
+template <int... O>
+FIF_DEV void store_bf16(__nv_bfloat16* dst, const float (&m)[kMom], float scale, int acc,
+                        std::integer_sequence<int, O...>) {
+    auto one = [&](__nv_bfloat16* d, float v) {
+        if (acc != 0) v = fmaf((float)acc, v, __bfloat162float(*d));
+        *d = __float2bfloat16_rn(v);
+    };
+    (one(dst + O, coef_of<O>(m) * scale), ...);
+}
+
+// the 21 entries of C_k (times scale)
+template <int K, int... E>
+FIF_DEV void coefs_k(const float (&m)[kMom], float scale, float (&C)[21], std::integer_sequence<int, E...>) {
+    ((C[E] = coef_of<21 * K + E>(m) * scale), ...);
+}
+
+// the paper's positional trace factor (Sec. VI-A-2): tr of the world-frame C_k,
+//   tr(M_c^T C M_c) = tr(A) + tr(D) + |c|^2 tr(A) - c^T A c + 2 tr([c]x B)
+template <int K>
+FIF_DEV float trace_k(const float (&m)[kMom], float scale, float cx, float cy, float cz) {
+    float C[21];
+    coefs_k<K>(m, scale, C, std::make_integer_sequence<int, 21>{});
+    float A[3][3], Bm[3][3], trD = 0.f;
+#pragma unroll
+    for (int e = 0; e < 21; ++e) {
+        const int r = sym_row(e), c = sym_col(e);
+        if (r < 3 && c < 3) { A[r][c] = C[e]; A[c][r] = C[e]; }
+        else if (r < 3) Bm[r][c - 3] = C[e];
+        else if (r == c) trD += C[e];
     }
-    const int ra = r - 3, cb = c - 3;
-    float v = -moment(hs, ls, tid, 0, mx + (ra == 0) + (cb == 0), my + (ra == 1) + (cb == 1), mz + (ra == 2) + (cb == 2));
-    if (ra == cb) v += moment(hs, ls, tid, 0, mx, my, mz);
-    return v;
+    const float c3[3] = {cx, cy, cz};
+    const float cc = cx * cx + cy * cy + cz * cz;
+    const float trA = A[0][0] + A[1][1] + A[2][2];
+    float cAc = 0.f, cxB = 0.f;
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) cAc += c3[r] * A[r][c] * c3[c];
+    // [c]x = [[0, -cz, cy], [cz, 0, -cx], [-cy, cx, 0]];  tr([c]x B) = sum_ij [c]x_ij B_ji
+    const float S[3][3] = {{0.f, -cz, cy}, {cz, 0.f, -cx}, {-cy, cx, 0.f}};
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) cxB += S[r][c] * Bm[c][r];
+    return trA + trD + cc * trA - cAc + 2.f * cxB;
+}
+
+template <int... K>
+FIF_DEV void traces(const float (&m)[kMom], float scale, float cx, float cy, float cz, float (&out)[10],
+                    std::integer_sequence<int, K...>) {
+    ((out[K] = trace_k<K>(m, scale, cx, cy, cz)), ...);
 }
 
 __global__ void __launch_bounds__(kThreads, 2) build_kernel(BuildArgs a) {
@@ -436,63 +551,21 @@ __global__ void __launch_bounds__(kThreads, 2) build_kernel(BuildArgs a) {
     if (a.accumulate != 0 && cand == 0) return;
     // ---- epilogue: 66 moments -> 210 coefficients (times 1/sigma^2) ----
     const int64_t node = ni + (int64_t)a.nx * (nj + (int64_t)a.ny * nk);
+    float m[kMom];
+#pragma unroll
+    for (int i = 0; i < kMom; ++i) m[i] = ok ? hs[i * kThreads + tid] - ls[i * kThreads + tid] : 0.f;
     if (a.storage == FIF_STORAGE_TRACE) {
-        // the paper's positional trace factor (Sec. VI-A-2): tr of the world-frame C_k,
-        //   tr(M_c^T C M_c) = tr(A) + tr(D) + |c|^2 tr(A) - c^T A c + 2 tr([c]x B)
         float* dst = reinterpret_cast<float*>(a.out) + node * a.stride;
-        const float c3[3] = {cx, cy, cz};
-        const float cc = cx * cx + cy * cy + cz * cz;
-        for (int k = 0; k < 10; ++k) {
-            float val = 0.f;
-            if (ok) {
-                float A[3][3], Bm[3][3], trD = 0.f;
-                for (int e = 0; e < 21; ++e) {
-                    const float v = coef_local(hs, ls, tid, k, e) * a.inv_sigma2;
-                    const int r = sym_row(e), c = sym_col(e);
-                    if (r < 3 && c < 3) { A[r][c] = v; A[c][r] = v; }
-                    else if (r < 3) Bm[r][c - 3] = v;
-                    else if (r == c) trD += v;
-                }
-                const float trA = A[0][0] + A[1][1] + A[2][2];
-                float cAc = 0.f, cxB = 0.f;
-                for (int r = 0; r < 3; ++r)
-                    for (int c = 0; c < 3; ++c) cAc += c3[r] * A[r][c] * c3[c];
-                // [c]x = [[0, -cz, cy], [cz, 0, -cx], [-cy, cx, 0]];  tr([c]x B) = sum_ij [c]x_ij B_ji
-                const float S[3][3] = {{0.f, -cz, cy}, {cz, 0.f, -cx}, {-cy, cx, 0.f}};
-                for (int r = 0; r < 3; ++r)
-                    for (int c = 0; c < 3; ++c) cxB += S[r][c] * Bm[c][r];
-                val = trA + trD + cc * trA - cAc + 2.f * cxB;
-            }
-            if (a.accumulate != 0) val = fmaf((float)a.accumulate, val, dst[k]);
-            dst[k] = val;
-        }
+        float tr[10];
+        traces(m, a.inv_sigma2, cx, cy, cz, tr, std::make_integer_sequence<int, 10>{});
+        for (int k = 0; k < 10; ++k) dst[k] = a.accumulate != 0 ? fmaf((float)a.accumulate, tr[k], dst[k]) : tr[k];
         for (int k = 10; k < a.stride; ++k) dst[k] = 0.f;
-        return;
-    }
-    float outv[4];
-    int filled = 0;
-    for (int o = 0; o < a.stride; ++o) {
-        float val = 0.f;
-        if (o < 210 && ok) val = coef_local(hs, ls, tid, o / 21, o % 21) * a.inv_sigma2;
-        if (a.storage == FIF_STORAGE_F32) {
-            outv[filled++] = val;
-            if (filled == 4) {
-                float4* dst = reinterpret_cast<float4*>(reinterpret_cast<float*>(a.out) + node * a.stride + (o - 3));
-                float4 v4 = make_float4(outv[0], outv[1], outv[2], outv[3]);
-                if (a.accumulate != 0) {
-                    const float sgn = (float)a.accumulate;
-                    const float4 old = *dst;
-                    v4 = make_float4(fmaf(sgn, v4.x, old.x), fmaf(sgn, v4.y, old.y), fmaf(sgn, v4.z, old.z),
-                                     fmaf(sgn, v4.w, old.w));
-                }
-                *dst = v4;
-                filled = 0;
-            }
-        } else {
-            __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(a.out) + node * a.stride + o;
-            if (a.accumulate != 0) val = fmaf((float)a.accumulate, val, __bfloat162float(*dst));
-            *dst = __float2bfloat16_rn(val);
-        }
+    } else if (a.storage == FIF_STORAGE_F32) {
+        float4* dst = reinterpret_cast<float4*>(reinterpret_cast<float*>(a.out) + node * a.stride);
+        store_f32(dst, m, a.inv_sigma2, a.accumulate, std::make_integer_sequence<int, 216 / 4>{});
+    } else {
+        __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(a.out) + node * a.stride;
+        store_bf16(dst, m, a.inv_sigma2, a.accumulate, std::make_integer_sequence<int, 224>{});
     }
 }
 
