@@ -12,9 +12,9 @@
 //             bin: by input index), so a brick of nodes reads only the landmarks whose bins
 //             come within r_max of it, as contiguous runs.
 //  build      one CTA = a brick of 8 x 4 x 4 nodes, one thread = one register-resident
-//             node.  Thread 0 streams the brick's candidate landmarks through a 3-slot ring
-//             of shared-memory tiles with bulk copies (cp.async.bulk + mbarrier); all 128
-//             threads read each landmark as a shared-memory broadcast.
+//             node.  A fifth warp streams the brick's candidate landmarks through a 3-slot
+//             ring of shared-memory tiles with bulk copies (cp.async.bulk + full/empty
+//             mbarriers); the 128 node threads read each landmark as a shared-memory broadcast.
 //
 // Arithmetic per (node, landmark): every entry of v_p[k] * I_i is a polynomial in u of
 // degree <= 4 times 1/n^2, 1/n or 1.  Because |u| = 1, multiplying by (u.u)^m raises any
@@ -163,7 +163,8 @@ struct BuildSmem {
     int tile_count[kSlots];
     uint16_t keep[kThreads / 32][kTile];   // per-warp list of the tile's landmarks near its sub-brick
     int nruns;
-    uint64_t bars[kSlots];
+    uint64_t full[kSlots];    // tile landed (producer arrival + copy bytes)
+    uint64_t empty[kSlots];   // every consumer warp is done with the tile
 };
 
 // ---- moments -> coefficients -----------------------------------------------------------
@@ -337,7 +338,7 @@ FIF_DEV void traces(const float (&m)[kMom], float scale, float cx, float cy, flo
     ((out[K] = trace_k<K>(m, scale, cx, cy, cz)), ...);
 }
 
-__global__ void __launch_bounds__(kThreads, 2) build_kernel(BuildArgs a) {
+__global__ void __launch_bounds__(kThreads + 32, 2) build_kernel(BuildArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     BuildSmem& S = *reinterpret_cast<BuildSmem*>(smem_raw);
     const int tid = threadIdx.x;
@@ -347,11 +348,13 @@ __global__ void __launch_bounds__(kThreads, 2) build_kernel(BuildArgs a) {
     const int brick = blockIdx.x;
     const int bxi = brick % nbx, byi = (brick / nbx) % nby, bzi = brick / (nbx * nby);
     const int i0 = bxi * kBX, j0 = byi * kBY, k0 = bzi * kBZ;
-    // warp w owns the 4 x 4 x 2 sub-brick at x offset 4 (w & 1), z offset 2 (w >> 1)
+    // consumer warp w < 4 owns the 4 x 4 x 2 sub-brick at x offset 4 (w & 1), z offset 2 (w >> 1);
+    // warp 4 streams the landmark tiles
     const int warp = tid >> 5, lane = tid & 31;
+    const bool producer = warp == kThreads / 32;
     const int ti = 4 * (warp & 1) + (lane & 3), tj = (lane >> 2) & 3, tk = 2 * (warp >> 1) + (lane >> 4);
     const int ni = i0 + ti, nj = j0 + tj, nk = k0 + tk;
-    const bool valid = ni < a.nx && nj < a.ny && nk < a.nz;
+    const bool valid = !producer && ni < a.nx && nj < a.ny && nk < a.nz;
     const float cx = __fadd_rn(a.ox, __fmul_rn(a.res, (float)ni));
     const float cy = __fadd_rn(a.oy, __fmul_rn(a.res, (float)nj));
     const float cz = __fadd_rn(a.oz, __fmul_rn(a.res, (float)nk));
@@ -367,7 +370,7 @@ __global__ void __launch_bounds__(kThreads, 2) build_kernel(BuildArgs a) {
     const float whi[3] = {a.ox + a.res * min(wi0 + 3, a.nx - 1), a.oy + a.res * min(j0 + kBY - 1, a.ny - 1),
                           a.oz + a.res * min(wk0 + 1, a.nz - 1)};
 
-    for (int idx = tid; idx < kMom * kThreads; idx += kThreads) {
+    for (int idx = tid; idx < kMom * kThreads; idx += kThreads + 32) {
         (&S.hi[0][0])[idx] = 0.f;
         (&S.lo[0][0])[idx] = 0.f;
     }
@@ -376,24 +379,37 @@ __global__ void __launch_bounds__(kThreads, 2) build_kernel(BuildArgs a) {
     const BinGrid& bg = a.bg;
     const float rc = a.rcull, rc2 = rc * rc;
     const int* startp = reinterpret_cast<const int*>(a.ws + a.lay.start);
-    const int nrows = enumerate_runs(bg, startp, blo, bhi, rc, S.runs, kMaxRuns, tid, kThreads, a.err);
+    const int nrows = enumerate_runs(bg, startp, blo, bhi, rc, S.runs, kMaxRuns, tid, kThreads + 32, a.err);
     if (tid == 0) {
         S.nruns = nrows;
-        for (int s = 0; s < kSlots; ++s) mbar_init(&S.bars[s], 1);
+        for (int s = 0; s < kSlots; ++s) {
+            mbar_init(&S.full[s], 1);
+            mbar_init(&S.empty[s], kThreads / 32);
+        }
         fence_mbar_init();
     }
     __syncthreads();
 
-    // ---- producer state (thread 0 only) ----
-    const float4* sorted = reinterpret_cast<const float4*>(a.ws + a.lay.sorted);
-    TileProducer<kTile> prod;
-    auto produce = [&](int slot) {
-        S.tile_count[slot] = prod.fill(S.tile[slot], S.runs, S.nruns, sorted, &S.bars[slot]);
-        mbar_arrive(&S.bars[slot]);
-    };
-    if (tid == 0) {
-        fence_proxy_async();
-        for (int s = 0; s < kSlots; ++s) produce(s);
+    // ---- producer warp (lane 0): refills a slot as soon as every consumer warp is done with it,
+    // so the consumer warps drift apart by up to kSlots tiles instead of meeting at a barrier ----
+    if (producer) {
+        if (lane == 0) {
+            const float4* sorted = reinterpret_cast<const float4*>(a.ws + a.lay.sorted);
+            TileProducer<kTile> prod;
+            for (int it = 0;; ++it) {
+                const int slot = it % kSlots;
+                if (it >= kSlots && !mbar_wait_bounded(&S.empty[slot], (uint32_t)((it / kSlots - 1) & 1))) {
+                    set_error(a.err, FIF_ETIMEOUT);
+                    break;
+                }
+                fence_proxy_async();   // the consumers' reads of the slot precede the new copies
+                const int cnt = prod.fill(S.tile[slot], S.runs, S.nruns, sorted, &S.full[slot]);
+                S.tile_count[slot] = cnt;
+                mbar_arrive(&S.full[slot]);
+                if (cnt == 0) break;   // the end marker; every copy issued is consumed before it
+            }
+        }
+        return;
     }
 
     // ---- consume ----
@@ -441,10 +457,9 @@ __global__ void __launch_bounds__(kThreads, 2) build_kernel(BuildArgs a) {
     for (int it = 0;; ++it) {
         const int slot = it % kSlots;
         const uint32_t par = (uint32_t)((it / kSlots) & 1);
-        const bool late = !mbar_wait_bounded(&S.bars[slot], par);
-        if (__syncthreads_or(late)) {  // every thread takes the same exit
+        if (__any_sync(0xffffffffu, !mbar_wait_bounded(&S.full[slot], par))) {  // the warp exits together
             ok = false;
-            if (tid == 0) set_error(a.err, FIF_ETIMEOUT);
+            if (lane == 0) set_error(a.err, FIF_ETIMEOUT);
             break;
         }
         const int cnt = S.tile_count[slot];
@@ -529,11 +544,8 @@ __global__ void __launch_bounds__(kThreads, 2) build_kernel(BuildArgs a) {
                 blk = 0;
             }
         }
-        __syncthreads();  // everyone is done with this slot
-        if (tid == 0) {
-            fence_proxy_async();
-            produce(slot);
-        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&S.empty[slot]);   // this warp is done with the slot
     }
     if (blk > 0) merge_block();
     // statistics
@@ -635,7 +647,7 @@ int launch_build(const BuildArgs& a, cudaStream_t stream) {
         return FIF_ECUDA;
     const int64_t bricks = (int64_t)((a.nx + kBX - 1) / kBX) * ((a.ny + kBY - 1) / kBY) * ((a.nz + kBZ - 1) / kBZ);
     if (bricks > (int64_t)INT32_MAX) return FIF_ERANGE;
-    build_kernel<<<(unsigned)bricks, kThreads, smem, stream>>>(a);
+    build_kernel<<<(unsigned)bricks, kThreads + 32, smem, stream>>>(a);
     return cudaPeekAtLastError() == cudaSuccess ? FIF_OK : FIF_ECUDA;
 }
 
