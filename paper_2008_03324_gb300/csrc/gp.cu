@@ -17,7 +17,8 @@
 // distinct banks), zero pads, stride = 21 rs rounded up to 4 floats.
 //
 // Build (gp_build_kernel): one CTA per 4 x 2 x 2 brick of nodes, one warp per node.  The
-// brick's candidate landmarks stream through a ring of shared-memory tiles (landmark_stream);
+// brick's candidate landmarks stream through a ring of shared-memory tiles (landmark_stream),
+// refilled by a 17th warp as soon as every node warp has released a slot;
 // each warp takes the exact single-precision shell decision for its node 32 landmarks at a
 // time, compacts the in-shell ones (u, 1/n) into a list, and every lane then accumulates, for
 // its sample axes g = lane + 32 k, the 15 moments
@@ -71,7 +72,8 @@ struct GpBuildSmem {
     int2 runs[kGbMaxRuns];
     int tile_count[kGbSlots];
     int nruns;
-    uint64_t bars[kGbSlots];
+    uint64_t full[kGbSlots];    // tile landed (producer arrival + copy bytes)
+    uint64_t empty[kGbSlots];   // every node warp is done with the tile
 };
 
 FIF_DEV float ex2_approx(float x) {
@@ -86,7 +88,7 @@ FIF_DEV float rcp_approx(float x) {
 }
 
 template <int G>
-__global__ void __launch_bounds__(kGbThreads, 1) gp_build_kernel(BuildArgs a) {
+__global__ void __launch_bounds__(kGbThreads + 32, 1) gp_build_kernel(BuildArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     GpBuildSmem<G>& S = *reinterpret_cast<GpBuildSmem<G>*>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -95,7 +97,8 @@ __global__ void __launch_bounds__(kGbThreads, 1) gp_build_kernel(BuildArgs a) {
     const int brick = blockIdx.x;
     const int i0 = 4 * (brick % nbx), j0 = 2 * ((brick / nbx) % nby), k0 = 2 * (brick / (nbx * nby));
     const int ni = i0 + (warp & 3), nj = j0 + ((warp >> 2) & 1), nk = k0 + (warp >> 3);
-    const bool valid = ni < a.nx && nj < a.ny && nk < a.nz;
+    const bool producer = warp == kGbWarps;   // the 17th warp streams the landmark tiles
+    const bool valid = !producer && ni < a.nx && nj < a.ny && nk < a.nz;
     const float cx = __fadd_rn(a.ox, __fmul_rn(a.res, (float)ni));
     const float cy = __fadd_rn(a.oy, __fmul_rn(a.res, (float)nj));
     const float cz = __fadd_rn(a.oz, __fmul_rn(a.res, (float)nk));
@@ -105,28 +108,42 @@ __global__ void __launch_bounds__(kGbThreads, 1) gp_build_kernel(BuildArgs a) {
 
     float* hs = &S.hi[0][0][0];
     float* ls = &S.lo[0][0][0];
-    for (int idx = tid; idx < kGbWarps * kGbMom * G * 32; idx += kGbThreads) {
+    for (int idx = tid; idx < kGbWarps * kGbMom * G * 32; idx += kGbThreads + 32) {
         hs[idx] = 0.f;
         ls[idx] = 0.f;
     }
     const int* startp = reinterpret_cast<const int*>(a.ws + a.lay.start);
-    const int nrows = enumerate_runs(a.bg, startp, blo, bhi, a.rcull, S.runs, kGbMaxRuns, tid, kGbThreads, a.err);
+    const int nrows =
+        enumerate_runs(a.bg, startp, blo, bhi, a.rcull, S.runs, kGbMaxRuns, tid, kGbThreads + 32, a.err);
     if (tid == 0) {
         S.nruns = nrows;
-        for (int s = 0; s < kGbSlots; ++s) mbar_init(&S.bars[s], 1);
+        for (int s = 0; s < kGbSlots; ++s) {
+            mbar_init(&S.full[s], 1);
+            mbar_init(&S.empty[s], kGbWarps);
+        }
         fence_mbar_init();
     }
     __syncthreads();
 
-    const float4* sorted = reinterpret_cast<const float4*>(a.ws + a.lay.sorted);
-    TileProducer<kGbTile> prod;
-    auto produce = [&](int slot) {
-        S.tile_count[slot] = prod.fill(S.tile[slot], S.runs, S.nruns, sorted, &S.bars[slot]);
-        mbar_arrive(&S.bars[slot]);
-    };
-    if (tid == 0) {
-        fence_proxy_async();
-        for (int s = 0; s < kGbSlots; ++s) produce(s);
+    // producer warp (lane 0): refills a slot as soon as every node warp is done with it
+    if (producer) {
+        if (lane == 0) {
+            const float4* sorted = reinterpret_cast<const float4*>(a.ws + a.lay.sorted);
+            TileProducer<kGbTile> prod;
+            for (int it = 0;; ++it) {
+                const int slot = it % kGbSlots;
+                if (it >= kGbSlots && !mbar_wait_bounded(&S.empty[slot], (uint32_t)((it / kGbSlots - 1) & 1))) {
+                    set_error(a.err, FIF_ETIMEOUT);
+                    break;
+                }
+                fence_proxy_async();   // the node warps' reads of the slot precede the new copies
+                const int cnt = prod.fill(S.tile[slot], S.runs, S.nruns, sorted, &S.full[slot]);
+                S.tile_count[slot] = cnt;
+                mbar_arrive(&S.full[slot]);
+                if (cnt == 0) break;   // the end marker; every copy issued is consumed before it
+            }
+        }
+        return;
     }
 
     // samples in the last slot of 32 axes, and landmarks it takes per pass (lane l of that slot:
@@ -200,10 +217,9 @@ __global__ void __launch_bounds__(kGbThreads, 1) gp_build_kernel(BuildArgs a) {
     for (int it = 0;; ++it) {
         const int slot = it % kGbSlots;
         const uint32_t par = (uint32_t)((it / kGbSlots) & 1);
-        const bool late = !mbar_wait_bounded(&S.bars[slot], par);
-        if (__syncthreads_or(late)) {
+        if (__any_sync(0xffffffffu, !mbar_wait_bounded(&S.full[slot], par))) {   // the warp exits together
             ok = false;
-            if (tid == 0) set_error(a.err, FIF_ETIMEOUT);
+            if (lane == 0) set_error(a.err, FIF_ETIMEOUT);
             break;
         }
         const int cnt = S.tile_count[slot];
@@ -287,11 +303,8 @@ __global__ void __launch_bounds__(kGbThreads, 1) gp_build_kernel(BuildArgs a) {
                 }
             }
         }
-        __syncthreads();
-        if (tid == 0) {
-            fence_proxy_async();
-            produce(slot);
-        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&S.empty[slot]);   // this warp is done with the slot
     }
     if (valid && inblock > 0) merge();
     __syncwarp();
@@ -872,7 +885,7 @@ static int launch_gp_build_g(const BuildArgs& a, cudaStream_t stream) {
         return FIF_ECUDA;
     const int64_t bricks = (int64_t)((a.nx + 3) / 4) * ((a.ny + 1) / 2) * ((a.nz + 1) / 2);
     if (bricks > (int64_t)INT32_MAX) return FIF_ERANGE;
-    gp_build_kernel<G><<<(unsigned)bricks, kGbThreads, smem, stream>>>(a);
+    gp_build_kernel<G><<<(unsigned)bricks, kGbThreads + 32, smem, stream>>>(a);
     return cudaPeekAtLastError() == cudaSuccess ? FIF_OK : FIF_ECUDA;
 }
 
