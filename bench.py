@@ -51,7 +51,7 @@ QUERY_TRAFFIC = {"bytes_per_pose": (29.014592e9 + 0.474674e9) / 4194304,
 # the same for the GP query (N_s = 70) from profiles/gp_query_kernel_warehouse_nz8.md
 # (read 11.723 GB + write 0.0115 GB for 262,144 poses on the 200 x 200 x 8 lattice)
 GP_QUERY_TRAFFIC = {"bytes_per_pose": (11.722679e9 + 0.011474e9) / 262144, "n_samples": 70,
-                    "digest": "3b92b808a537f057"}
+                    "digest": "d7b567bfb4d07592"}
 # FMA-pipe utilisation of build_kernel (ncu sm__pipe_fma_cycles_active, profiles/build_kernel_warehouse_nz8.md),
 # valid while the build sources hash to the recorded digest
 BUILD_PIPE = {"fma_pipe_active": 0.656, "digest": "05668e59f8af29ff"}
@@ -294,7 +294,7 @@ def gp_block(fif, synth, spec, lm, r_max, m, ns, dev, stream, hbm_peak, build_st
                               "frac": ach / hbm_peak,
                               "traffic": (GP_QUERY_TRAFFIC["bytes_per_pose"] * m
                                           if ns == GP_QUERY_TRAFFIC["n_samples"] and GP_QUERY_TRAFFIC["digest"] ==
-                                          query_source_digest(("gp.cu", "fif_common.cuh")) else None)}}
+                                          query_source_digest(("gp_query.cu", "fif_common.cuh")) else None)}}
     del fgp, ws, poses
     torch.cuda.empty_cache()
     return out
