@@ -54,7 +54,7 @@ GP_QUERY_TRAFFIC = {"bytes_per_pose": (11.722679e9 + 0.011474e9) / 262144, "n_sa
                     "digest": "d7b567bfb4d07592"}
 # FMA-pipe utilisation of build_kernel (ncu sm__pipe_fma_cycles_active, profiles/build_kernel_warehouse_nz8.md),
 # valid while the build sources hash to the recorded digest
-BUILD_PIPE = {"fma_pipe_active": 0.656, "digest": "05668e59f8af29ff"}
+BUILD_PIPE = {"fma_pipe_active": 0.679, "digest": "598e801891ee396e"}
 # GP build, per (in-shell pair, sample axis): sigmoid 10 (dot 6, shift 1, exp 1, add 1, rcp 1)
 # + 15 moment accumulations 30; per pair: bearing products 16
 GP_FLOPS_PER_PAIR_SAMPLE = 40
