@@ -23,7 +23,8 @@
 //  weights  (8 warps)  K_z in double-float arithmetic, a(z) = W K_z as compensated
 //                      single-precision sums with W split into high and low parts
 //                      (two-product / two-sum);
-//  metric   (2 warps)  one per buffer of the corner table, lane = pose: moves the 8 corner
+//  metric   (2 or 4)   one per buffer of the corner table (4 buffers up to N_s = 64, when
+//                      they fit), lane = pose: moves the 8 corner
 //                      matrices from their nodes to the camera position, sums, rotates into the
 //                      camera frame, and reduces to trace / log|det| / lambda_min as the
 //                      quadratic query does.
@@ -42,34 +43,33 @@ namespace {
 // ------------------------------------------------------------------------------------
 constexpr int kGqContract = 4;                 // one warp per x-adjacent corner pair
 constexpr int kGqWeights = 8;                  // one block of kGqPB poses per group each
-constexpr int kGqMetric = 2;                   // metric warp m finishes the groups of table buffer m
-constexpr int kGqWarps = kGqContract + kGqWeights + kGqMetric;
-constexpr int kGqThreads = kGqWarps * 32;
+constexpr int kGqMaxNB = 4;                    // table buffers (= metric warps) at most
 constexpr int kGqPB = 4;                       // poses per weights block
 constexpr int kEbRow = 169;                    // floats per pose in the corner table (odd)
 constexpr int kGqMaxStages = 4;
 
 struct GqLayout {
-    int ring, atab, eb, kbuf, ptab, wsm, tab, bars, flag, total, stages;
+    int ring, atab, eb, kbuf, ptab, wsm, tab, bars, flag, total, stages, nb;
     int w_smem;   // 1: W is staged in shared memory at wsm; 0: read from global memory
 };
 
 // shared-memory layout for S floats per node, row stride rs, N_s samples, `stages` ring slots per
-// contract warp, W in shared memory or not
-__host__ __device__ inline GqLayout gq_layout(int S, int rs, int ns, int stages, int w_smem) {
+// contract warp, W in shared memory or not, nb buffers of the weights and corner tables
+__host__ __device__ inline GqLayout gq_layout(int S, int rs, int ns, int stages, int w_smem, int nb) {
     GqLayout L;
     int off = 0;
     L.stages = stages;
     L.w_smem = w_smem;
+    L.nb = nb;
     L.ring = off;  off += kGqContract * stages * 2 * S * 4;
-    L.atab = off;  off += 2 * 32 * rs * 4;
-    L.eb = off;    off += 2 * 32 * kEbRow * 4;
+    L.atab = off;  off += nb * 32 * rs * 4;
+    L.eb = off;    off += nb * 32 * kEbRow * 4;
     off = (off + 15) / 16 * 16;
     L.kbuf = off;  off += kGqWeights * (kGqPB / 2) * rs * 16;
     L.ptab = off;  off += kGqContract * 2 * 32 * 16;
     L.wsm = off;   off += w_smem ? ns * rs * 8 : 0;
     L.tab = off;   off += 18 * 16;
-    L.bars = off;  off += (kGqContract * kGqMaxStages + 8) * 8;
+    L.bars = off;  off += (kGqContract * kGqMaxStages + 4 * kGqMaxNB) * 8;
     L.flag = off;  off += 16;
     L.total = (off + 127) / 128 * 128;
     return L;
@@ -77,7 +77,7 @@ __host__ __device__ inline GqLayout gq_layout(int S, int rs, int ns, int stages,
 
 struct GqBars {
     uint64_t full[kGqContract][kGqMaxStages];
-    uint64_t aready[2], afree[2], efull[2], eempty[2];
+    uint64_t aready[kGqMaxNB], afree[kGqMaxNB], efull[kGqMaxNB], eempty[kGqMaxNB];
 };
 
 // lattice cell and trilinear weights of a position (the same arithmetic as query.cu)
@@ -229,8 +229,10 @@ FIF_DEV void df_fma2(float2 Wh, float2 Whn, float2 Wl, float2 Kh, float2 Kl, flo
     lo = add2(lo, add2(err, e));
 }
 
-template <int G>
-__global__ void __launch_bounds__(kGqThreads, 1) gp_query_kernel(QueryArgs a, GqLayout L) {
+// NB table buffers and as many metric warps: group k uses buffer k mod NB
+template <int G, int NB>
+__global__ void __launch_bounds__((kGqContract + kGqWeights + NB) * 32, 1) gp_query_kernel(QueryArgs a, GqLayout L) {
+    constexpr int kThreads = (kGqContract + kGqWeights + NB) * 32;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float* ring = reinterpret_cast<float*>(smem_raw + L.ring);
     float* atab = reinterpret_cast<float*>(smem_raw + L.atab);
@@ -250,7 +252,7 @@ __global__ void __launch_bounds__(kGqThreads, 1) gp_query_kernel(QueryArgs a, Gq
     if (threadIdx.x == 0) {
         for (int j = 0; j < kGqContract; ++j)
             for (int s = 0; s < kGqMaxStages; ++s) mbar_init(&B.full[j][s], 1);
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < NB; ++b) {
             mbar_init(&B.aready[b], kGqWeights);
             mbar_init(&B.afree[b], kGqContract);
             mbar_init(&B.efull[b], kGqContract);
@@ -259,10 +261,10 @@ __global__ void __launch_bounds__(kGqThreads, 1) gp_query_kernel(QueryArgs a, Gq
         *flag = 0;
         fence_mbar_init();
     }
-    for (int idx = threadIdx.x; idx < 2 * 32 * rs; idx += kGqThreads) atab[idx] = 0.f;   // pads stay zero
+    for (int idx = threadIdx.x; idx < NB * 32 * rs; idx += kThreads) atab[idx] = 0.f;   // pads stay zero
     if (L.w_smem)
-        for (int idx = threadIdx.x; idx < ns * rs; idx += kGqThreads) wsm[idx] = __ldg(a.gp_wt + idx);
-    for (int idx = threadIdx.x; idx < 18; idx += kGqThreads) ctab[idx] = __ldg(a.gp_consts + idx);
+        for (int idx = threadIdx.x; idx < ns * rs; idx += kThreads) wsm[idx] = __ldg(a.gp_wt + idx);
+    for (int idx = threadIdx.x; idx < 18; idx += kThreads) ctab[idx] = __ldg(a.gp_consts + idx);
     __syncthreads();
 
     if (warp < kGqContract) {
@@ -313,11 +315,12 @@ __global__ void __launch_bounds__(kGqThreads, 1) gp_query_kernel(QueryArgs a, Gq
             if (p < 0 || *flag) break;
             const int64_t k = it >> 5;
             const int i = (int)(it & 31);
-            const int b = (int)(k & 1);
+            const int b = (int)(k % NB);
+            const uint32_t use = (uint32_t)((k / NB) & 1);
             if (i == 0) {
                 if ((int64_t)blockIdx.x + (k + 1) * (int64_t)gridDim.x < groups) fill_table(k + 1);
-                if (!gq_wait(&B.aready[b], (uint32_t)((k >> 1) & 1), flag, a.err)) break;
-                if (k >= 2 && !gq_wait(&B.eempty[b], (uint32_t)(((k >> 1) & 1) ^ 1), flag, a.err)) break;
+                if (!gq_wait(&B.aready[b], use, flag, a.err)) break;
+                if (k >= NB && !gq_wait(&B.eempty[b], use ^ 1u, flag, a.err)) break;
             }
             if (lane == 0) issue(it + NS - 1);
             if (!gq_wait(&B.full[jp][it % NS], (uint32_t)((it / NS) & 1), flag, a.err)) break;
@@ -370,8 +373,8 @@ __global__ void __launch_bounds__(kGqThreads, 1) gp_query_kernel(QueryArgs a, Gq
         for (int64_t k = 0;; ++k) {
             const int64_t g = (int64_t)blockIdx.x + k * gridDim.x;
             if (g >= groups || *flag) break;
-            const int b = (int)(k & 1);
-            if (k >= 2 && !gq_wait(&B.afree[b], (uint32_t)(((k >> 1) & 1) ^ 1), flag, a.err)) break;
+            const int b = (int)(k % NB);
+            if (k >= NB && !gq_wait(&B.afree[b], (uint32_t)((k / NB) & 1) ^ 1u, flag, a.err)) break;
             const int cnt = (m - g * 32 < 32) ? (int)(m - g * 32) : 32;
             for (int i0 = w * kGqPB; i0 < cnt; i0 += kGqWeights * kGqPB) {
                 // optical axes of the block's poses: normalised in double precision (as the
@@ -472,11 +475,11 @@ __global__ void __launch_bounds__(kGqThreads, 1) gp_query_kernel(QueryArgs a, Gq
     } else {
         // ================================ metric warp ================================
         const int mw = warp - kGqContract - kGqWeights;   // = the table buffer it serves
-        for (int64_t k = mw;; k += kGqMetric) {
+        for (int64_t k = mw;; k += NB) {
             const int64_t g = (int64_t)blockIdx.x + k * gridDim.x;
             if (g >= groups || *flag) break;
-            const int b = (int)(k & 1);
-            if (!gq_wait(&B.efull[b], (uint32_t)((k >> 1) & 1), flag, a.err)) break;
+            const int b = (int)(k % NB);
+            if (!gq_wait(&B.efull[b], (uint32_t)((k / NB) & 1), flag, a.err)) break;
             const int cnt = (m - g * 32 < 32) ? (int)(m - g * 32) : 32;
             if (lane < cnt) {
                 const int64_t p = g * 32 + lane;
@@ -561,29 +564,43 @@ __global__ void __launch_bounds__(kGqThreads, 1) gp_query_kernel(QueryArgs a, Gq
 
 }  // namespace
 
+template <int G, int NB>
+static int launch_gp_query_nb(const QueryArgs& a, const GqLayout& L, int sms, cudaStream_t stream) {
+    if (cudaFuncSetAttribute(gp_query_kernel<G, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total) !=
+        cudaSuccess)
+        return FIF_ECUDA;
+    const int64_t groups = (a.m + 31) / 32;
+    const int64_t grid = std::min<int64_t>(groups, (int64_t)sms);
+    if (grid <= 0) return FIF_OK;
+    gp_query_kernel<G, NB><<<(unsigned)grid, (kGqContract + kGqWeights + NB) * 32, L.total, stream>>>(a, L);
+    return cudaPeekAtLastError() == cudaSuccess ? FIF_OK : FIF_ECUDA;
+}
+
 template <int G>
 static int launch_gp_query_g(const QueryArgs& a, cudaStream_t stream) {
     int dev = 0, sms = 0, max_smem = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    // prefer W in shared memory (its reads sit on the weights warps' critical path), then as
-    // many ring stages as fit (at least 2); without room for W, read it from global memory
+    // Up to 64 samples the per-pose metric work outweighs the gather: four table buffers and
+    // four metric warps, if W fits in shared memory beside at least 3 ring stages.  Otherwise two
+    // buffers; prefer W in shared memory (its reads sit on the weights warps' critical path),
+    // then as many ring stages as fit (at least 2); without room for W, read it from global memory.
     GqLayout L;
+    if constexpr (G < 3) {
+        for (int stages = kGqMaxStages; stages >= 3; --stages) {
+            L = gq_layout(a.stride, a.gp_rs, a.gp_ns, stages, 1, 4);
+            if (L.total <= max_smem) return launch_gp_query_nb<G, 4>(a, L, sms, stream);
+        }
+    }
     bool found = false;
     for (int w_smem = 1; w_smem >= 0 && !found; --w_smem)
         for (int stages = kGqMaxStages; stages >= 2 && !found; --stages) {
-            L = gq_layout(a.stride, a.gp_rs, a.gp_ns, stages, w_smem);
+            L = gq_layout(a.stride, a.gp_rs, a.gp_ns, stages, w_smem, 2);
             found = L.total <= max_smem;
         }
     if (!found) return FIF_ERANGE;
-    if (cudaFuncSetAttribute(gp_query_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total) != cudaSuccess)
-        return FIF_ECUDA;
-    const int64_t groups = (a.m + 31) / 32;
-    const int64_t grid = std::min<int64_t>(groups, (int64_t)sms);
-    if (grid <= 0) return FIF_OK;
-    gp_query_kernel<G><<<(unsigned)grid, kGqThreads, L.total, stream>>>(a, L);
-    return cudaPeekAtLastError() == cudaSuccess ? FIF_OK : FIF_ECUDA;
+    return launch_gp_query_nb<G, 2>(a, L, sms, stream);
 }
 
 int launch_gp_query(const QueryArgs& a, cudaStream_t stream) {
