@@ -49,9 +49,9 @@ BUILD_FLOPS_PER_PAIR = 151   # shell test 8, rsqrt 1, bearing 4, monomials 31, 6
 QUERY_TRAFFIC = {"bytes_per_pose": (29.014592e9 + 0.474674e9) / 4194304,
                  "digest": "7307f54a5e67b276"}
 # the same for the GP query (N_s = 70) from profiles/gp_query_kernel_warehouse_nz8.md
-# (read 11.723 GB + write 0.0115 GB for 262,144 poses on the 200 x 200 x 8 lattice)
-GP_QUERY_TRAFFIC = {"bytes_per_pose": (11.722679e9 + 0.011474e9) / 262144, "n_samples": 70,
-                    "digest": "d7b567bfb4d07592"}
+# (read 11.724 GB + write 0.0118 GB for 262,144 poses on the 200 x 200 x 8 lattice)
+GP_QUERY_TRAFFIC = {"bytes_per_pose": (11.723970e9 + 0.011759e9) / 262144, "n_samples": 70,
+                    "digest": "74ef5490899859da"}
 # FMA-pipe utilisation of build_kernel (ncu sm__pipe_fma_cycles_active, profiles/build_kernel_warehouse_nz8.md),
 # valid while the build sources hash to the recorded digest
 BUILD_PIPE = {"fma_pipe_active": 0.679, "digest": "598e801891ee396e"}
