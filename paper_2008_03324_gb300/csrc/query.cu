@@ -518,7 +518,7 @@ int launch_query_cfg(const QueryArgs& a, cudaStream_t stream) {
 
 int launch_query(const QueryArgs& a, cudaStream_t stream) {
     if (a.storage == FIF_STORAGE_BF16) return launch_query_cfg<2, 8, 4, 3, 4>(a, stream);
-    return launch_query_cfg<4, 6, 6, kStages, kPrefetch>(a, stream);
+    return launch_query_cfg<4, kGather, kMetric, kStages, kPrefetch>(a, stream);
 }
 
 }  // namespace fif
