@@ -302,7 +302,8 @@ FIF_API size_t fif_query_host_staging_bytes(int64_t chunk);
 /* fif_query over HOST buffers.  h_poses (float32[m][7]) and the outputs h_fim, h_metrics,
  * h_sign, h_status (layouts and NULL meaning as for fif_query) are host memory; page-locked
  * memory lets the copies run asynchronously and overlap the queries.  The poses go through
- * the device in chunks of `chunk` poses, double-buffered in d_staging (caller-owned, at least
+ * the device in pieces of at most `chunk` poses (a quarter chunk first and last, to shorten the
+ * copies not overlapped by a query), double-buffered in d_staging (caller-owned, at least
  * fif_query_host_staging_bytes(chunk) bytes, 16-byte aligned): chunk c's host-to-device copy
  * and chunk c-1's device-to-host copy run on copy_stream while chunk c-1 or c is queried on
  * `stream`, ordered by events (created and released inside the call); the first copy waits for

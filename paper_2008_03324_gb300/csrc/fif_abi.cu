@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "fif_internal.h"
 
@@ -346,11 +347,25 @@ int32_t fif_query_host(const fif_field* field, const float* h_poses, int64_t m, 
         ok = ok && cudaEventCreateWithFlags(&qd[b], cudaEventDisableTiming) == cudaSuccess;
     }
     ok = ok && cudaEventCreateWithFlags(&done, cudaEventDisableTiming) == cudaSuccess;
-    const int64_t nch = (m + chunk - 1) / chunk;
-    auto count = [&](int64_t c) { return std::min<int64_t>(chunk, m - c * chunk); };
+    // pieces of the batch: a quarter chunk first and last (less copy time before the first query
+    // and after the last one), full chunks between; every piece fits a staging buffer
+    std::vector<int64_t> piece{0};
+    if (m > chunk) {
+        const int64_t q = std::max<int64_t>(1, chunk / 4);
+        int64_t pos = q;
+        piece.push_back(pos);
+        while (m - pos > chunk + q) {
+            pos += chunk;
+            piece.push_back(pos);
+        }
+        if (m - pos > q) piece.push_back(m - q);
+    }
+    piece.push_back(m);
+    const int64_t nch = (int64_t)piece.size() - 1;
+    auto count = [&](int64_t c) { return piece[c + 1] - piece[c]; };
     auto upload = [&](int64_t c) {
         const int b = (int)(c & 1);
-        ok = ok && cudaMemcpyAsync(base[b] + L.poses, h_poses + c * chunk * 7, (size_t)count(c) * 7 * sizeof(float),
+        ok = ok && cudaMemcpyAsync(base[b] + L.poses, h_poses + piece[c] * 7, (size_t)count(c) * 7 * sizeof(float),
                                    cudaMemcpyHostToDevice, sc) == cudaSuccess;
         ok = ok && cudaEventRecord(h2d[b], sc) == cudaSuccess;
     };
@@ -360,7 +375,7 @@ int32_t fif_query_host(const fif_field* field, const float* h_poses, int64_t m, 
     if (ok) upload(0);
     for (int64_t c = 0; c < nch && ok; ++c) {
         const int b = (int)(c & 1);
-        const int64_t n = count(c), p0 = c * chunk;
+        const int64_t n = count(c), p0 = piece[c];
         unsigned char* B = base[b];
         ok = cudaStreamWaitEvent(sq, h2d[b], 0) == cudaSuccess;
         if (!ok) break;
