@@ -44,10 +44,10 @@ WORKLOAD = ("warehouse 50x50x10 m, 200k landmarks (60% box faces / 40% walls, 40
 QUERY_BYTES_PER_POSE = 8 * 210 * 4 + 7 * 4 + 21 * 4 + 3 * 8 + 1 + 4   # corners + pose + outputs
 BUILD_FLOPS_PER_PAIR = 151   # shell test 8, rsqrt 1, bearing 4, monomials 31, 66 accumulations 107
 # DRAM traffic of one query launch per pose, from the ncu capture summarised in
-# profiles/query_kernel_warehouse_4M.md (read 29.015 GB + write 0.475 GB for 4,194,304 poses),
+# profiles/query_kernel_warehouse_4M.md (read 29.017 GB + write 0.475 GB for 4,194,304 poses),
 # valid while the kernel sources hash to the recorded digest
-QUERY_TRAFFIC = {"bytes_per_pose": (29.014592e9 + 0.474674e9) / 4194304,
-                 "digest": "7307f54a5e67b276"}
+QUERY_TRAFFIC = {"bytes_per_pose": (29.016678e9 + 0.475145e9) / 4194304,
+                 "digest": "cd3b4e4e7a2dfbb8"}
 # the same for the GP query (N_s = 70) from profiles/gp_query_kernel_warehouse_nz8.md
 # (read 11.724 GB + write 0.0118 GB for 262,144 poses on the 200 x 200 x 8 lattice)
 GP_QUERY_TRAFFIC = {"bytes_per_pose": (11.723970e9 + 0.011759e9) / 262144, "n_samples": 70,
