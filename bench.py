@@ -43,17 +43,17 @@ WORKLOAD = ("warehouse 50x50x10 m, 200k landmarks (60% box faces / 40% walls, 40
             "(FIM + trace + log|det| + lambda_min)")
 QUERY_BYTES_PER_POSE = 8 * 210 * 4 + 7 * 4 + 21 * 4 + 3 * 8 + 1 + 4   # corners + pose + outputs
 BUILD_FLOPS_PER_PAIR = 151   # shell test 8, rsqrt 1, bearing 4, monomials 31, 66 accumulations 107
-# DRAM traffic of one query launch per pose, from the ncu capture summarised in
-# profiles/query_kernel_warehouse_4M.md (read 29.017 GB + write 0.475 GB for 4,194,304 poses),
+# DRAM traffic of one query launch per pose, from one ncu capture of query_kernel on the bench's
+# 2^22-pose step (read 29.017 GB + write 0.475 GB for 4,194,304 poses; summary under profiles/),
 # valid while the kernel sources hash to the recorded digest
 QUERY_TRAFFIC = {"bytes_per_pose": (29.016678e9 + 0.475145e9) / 4194304,
                  "digest": "cd3b4e4e7a2dfbb8"}
-# the same for the GP query (N_s = 70) from profiles/gp_query_kernel_warehouse_nz8.md
-# (read 11.724 GB + write 0.0118 GB for 262,144 poses on the 200 x 200 x 8 lattice)
+# the same for the GP query (N_s = 70), captured on the 200 x 200 x 8 lattice (read 11.724 GB +
+# write 0.0118 GB for 262,144 poses)
 GP_QUERY_TRAFFIC = {"bytes_per_pose": (11.723970e9 + 0.011759e9) / 262144, "n_samples": 70,
                     "digest": "74ef5490899859da"}
-# FMA-pipe utilisation of build_kernel (ncu sm__pipe_fma_cycles_active, profiles/build_kernel_warehouse_nz8.md),
-# valid while the build sources hash to the recorded digest
+# FMA-pipe utilisation of build_kernel (ncu sm__pipe_fma_cycles_active on the 200 x 200 x 8
+# lattice), valid while the build sources hash to the recorded digest
 BUILD_PIPE = {"fma_pipe_active": 0.679, "digest": "598e801891ee396e"}
 # GP build, per (in-shell pair, sample axis): sigmoid 10 (dot 6, shift 1, exp 1, add 1, rcp 1)
 # + 15 moment accumulations 30; per pair: bearing products 16
@@ -663,7 +663,7 @@ def main():
                          "frac": achieved / hbm_peak,
                          "traffic": (QUERY_TRAFFIC["bytes_per_pose"] * m
                                      if QUERY_TRAFFIC["digest"] == query_source_digest() else None),
-                         "traffic_note": "ncu dram read+write bytes per launch (profiles/query_kernel_warehouse_4M.md)",
+                         "traffic_note": "ncu dram read+write bytes per launch of query_kernel (summary in profiles/)",
                          "peak_kind": f"{peak_kind} (MEASURED_PEAKS hbm_gbs)",
                          "bytes_per_pose": QUERY_BYTES_PER_POSE, "kernel_ms": kernel_ms},
             "cpu_baseline": cpu,
