@@ -121,3 +121,20 @@ def local_to_world(F_local, spec):
     S[:, 1, 0], S[:, 2, 0], S[:, 2, 1] = c[:, 2], -c[:, 1], c[:, 0]
     M[:, :3, 3:] = -S
     return np.einsum("nji,nkjl,nlm->nkim", M, F_local, M)
+
+
+def build_c_client(out_dir):
+    """Compile tests/abi_client.c, a plain C program against include/fif.h, and link it with the
+    in-tree libfif.so and the CUDA runtime; returns the executable's path."""
+    import os
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    pkg = os.path.join(root, "paper_2008_03324_gb300")
+    cuda = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+    exe = os.path.join(str(out_dir), "abi_client")
+    cmd = ["gcc", "-std=c11", "-O2", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(root, "include"),
+           "-I", os.path.join(cuda, "include"), os.path.join(root, "tests", "abi_client.c"), "-o", exe,
+           "-L", pkg, "-lfif", f"-Wl,-rpath,{pkg}", "-L", os.path.join(cuda, "lib64"), "-lcudart",
+           f"-Wl,-rpath,{os.path.join(cuda, 'lib64')}", "-lm"]
+    subprocess.run(cmd, check=True, capture_output=True, text=True)
+    return exe

@@ -135,3 +135,11 @@ def test_query_host_checks_and_staging_size(F):
     assert q(ctypes.byref(f), fake, 5, F.Q_METRICS, None, fake, None, None, 64, fake, need - 1, s1, s2) == F.ESIZE
     assert q(ctypes.byref(f), fake, 5, F.Q_METRICS, None, fake, None, None, 64, ctypes.c_void_p(0x100004), need,
              s1, s2) == F.EALIGN
+
+
+def test_c_client_compiles_and_links(F, tmp_path):
+    """include/fif.h is plain C and libfif.so links from a C program (no Python, no PyTorch); the
+    GPU tests run the same program."""
+    from tests import _fixtures as X
+    exe = X.build_c_client(tmp_path)
+    assert os.access(exe, os.X_OK)

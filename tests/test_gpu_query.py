@@ -236,3 +236,13 @@ def test_fma_probe_runs(F):
         assert bool(torch.isfinite(sink).all())
     assert F.lib().fif_fma_probe(None, 4, 10, 0, None) == F.EINVAL
     assert F.lib().fif_fma_probe(sink.data_ptr(), 4, 0, 0, None) == F.EINVAL
+
+
+def test_c_client_runs(F, tmp_path):
+    """A plain C client of the library (tests/abi_client.c) builds a field, queries it through
+    host and device buffers, and finds the two bitwise equal."""
+    import subprocess
+    exe = X.build_c_client(tmp_path)
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    assert "abi client ok" in r.stdout
