@@ -221,7 +221,7 @@ def run_reference(args):
     O.build()
     spec = synth.WAREHOUSE_GRID
     scene = synth.warehouse(seed=2, n=200_000)
-    n_poses = 128
+    n_poses = args.ref_poses
     poses = synth.random_poses(7, n_poses, spec.lo, spec.hi)
     grid = O.make_grid(spec.origin, spec.res, spec.dims)
     prm = O.make_params(r_max=10.0, v_alpha=0.5)
@@ -376,6 +376,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 2M-landmark building map")
     ap.add_argument("--serve-requests", type=int, default=1500)
+    ap.add_argument("--ref-poses", type=int, default=1024,
+                    help="poses per step of the reference arm (the FP64 oracle on the host cores)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
