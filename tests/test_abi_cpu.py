@@ -143,3 +143,19 @@ def test_c_client_compiles_and_links(F, tmp_path):
     from tests import _fixtures as X
     exe = X.build_c_client(tmp_path)
     assert os.access(exe, os.X_OK)
+
+
+def test_field_load_rejects_bad_files_before_any_copy(F, tmp_path):
+    """fif_field_load validates the file (magic, version, sizes, checksum) before it touches the
+    device: a foreign file, a truncated header and an empty file give FIF_EFORMAT; a missing file
+    FIF_EIO."""
+    lib = F.lib()
+    fake = ctypes.c_void_p(0x100000)
+    f = F.FieldC()
+    cases = {"foreign.fif": b"NOTAFIELD" + bytes(200), "short.fif": b"FIFFIELD" + bytes(8), "empty.fif": b""}
+    for name, data in cases.items():
+        p = tmp_path / name
+        p.write_bytes(data)
+        assert lib.fif_field_load(ctypes.byref(f), str(p).encode(), fake, 1 << 20, None, None) == F.EFORMAT, name
+    assert lib.fif_field_load(ctypes.byref(f), str(tmp_path / "none.fif").encode(), fake, 1 << 20, None,
+                              None) == F.EIO

@@ -246,3 +246,33 @@ def test_c_client_runs(F, tmp_path):
     r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stderr
     assert "abi client ok" in r.stdout
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_field_save_load_round_trip(F, tmp_path, storage):
+    """fif_field_save / fif_field_load (the field as a file: header + coefficient blob + checksum):
+    the loaded field has the same coefficients and answers queries bitwise alike; a corrupted
+    payload is refused."""
+    field = uploaded_room_field(F, storage=storage)
+    path = str(tmp_path / "room.fif")
+    F.field_save(field.c, path)
+    coeffs = torch.empty_like(field.coeffs)
+    fc = F.field_load(path, coeffs)
+    torch.cuda.synchronize()
+    assert torch.equal(coeffs, field.coeffs)
+    assert fc.storage == field.c.storage and fc.stride == field.c.stride
+    p = torch.from_numpy(np.ascontiguousarray(X.room_poses(200), np.float32)).cuda()
+    outs = []
+    for fcs in (field.c, fc):
+        met = torch.empty(200, 3, dtype=torch.float64, device="cuda")
+        fim = torch.empty(200, 21, device="cuda")
+        F.query(fcs, p, F.Q_METRICS, fim, met, None, None)
+        outs.append((fim.cpu(), met.cpu()))
+    torch.cuda.synchronize()
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+    data = bytearray(open(path, "rb").read())
+    data[-1] ^= 0xFF
+    bad = str(tmp_path / "bad.fif")
+    open(bad, "wb").write(bytes(data))
+    with pytest.raises(F.FifError):
+        F.field_load(bad, coeffs)
