@@ -24,8 +24,8 @@
 // and the hot loop accumulates only those 66 (31 monomials + 66 FMA/FADD per pair).
 // Accumulation is compensated: a block of 64 pairs (carried across tiles) is summed in
 // registers, then the block sum is added to a Kahan (sum, compensation) pair held in shared
-// memory.  The
-// epilogue expands the 66 moments into the 210 stored coefficients.
+// memory.  The epilogue expands the 66 moments into the 210 stored coefficients through the
+// integer map above, enumerated at compile time.
 #include "fif_common.cuh"
 #include "fif_internal.h"
 #include "landmark_stream.cuh"

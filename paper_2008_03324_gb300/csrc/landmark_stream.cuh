@@ -3,8 +3,9 @@
 //
 // The landmarks are counting-sorted into cubic bins (build.cu); the bins whose cells come
 // within the cull radius of a box of nodes form one contiguous run of the sorted array per bin
-// row (fixed y, z).  One thread fills shared-memory tiles from that run list with bulk copies
-// (cp.async.bulk) completing on an mbarrier; the CTA consumes the tiles in order.
+// row (fixed y, z).  One thread (lane 0 of a dedicated producer warp) fills shared-memory tiles
+// from that run list with bulk copies (cp.async.bulk) completing on a slot's "full" mbarrier;
+// the consumer warps read the tiles in order and release each slot on its "empty" mbarrier.
 #pragma once
 
 #include "fif_common.cuh"
