@@ -41,7 +41,12 @@ WORKLOAD = ("warehouse 50x50x10 m, 200k landmarks (60% box faces / 40% walls, 40
             "field 200x200x40 nodes @0.25 m (1.6M nodes, fp32 216/node), r in (0.1, 10] m, "
             "FoV 90 deg, v_alpha 0.5; step = fif_query of 2^22 uniform-random poses "
             "(FIM + trace + log|det| + lambda_min)")
-QUERY_BYTES_PER_POSE = 8 * 210 * 4 + 7 * 4 + 21 * 4 + 3 * 8 + 1 + 4   # corners + pose + outputs
+# algorithmic bytes of one pose's query: the 8 corner coefficient sets (210 floats each); the pose
+# and the outputs are reported beside it
+QUERY_BYTES_PER_POSE = 8 * 210 * 4
+QUERY_IO_BYTES_PER_POSE = 7 * 4 + 21 * 4 + 3 * 8 + 1 + 4    # pose in; FIM, metrics, sign, status out
+BF16_QUERY_BYTES_PER_POSE = 8 * 210 * 2
+TRACE_QUERY_BYTES_PER_POSE = 8 * 10 * 4
 BUILD_FLOPS_PER_PAIR = 151   # shell test 8, rsqrt 1, bearing 4, monomials 31, 66 accumulations 107
 # DRAM traffic of one query launch per pose, from one ncu capture of query_kernel on the bench's
 # 2^22-pose step (read 29.017 GB + write 0.475 GB for 4,194,304 poses; summary under profiles/),
@@ -63,6 +68,7 @@ SMS = 152
 FP32_LANES = 128
 SM_MAX_MHZ = 2070.0
 E2E_CHUNK = int(os.environ.get("FIF_E2E_CHUNK", 1 << 20))   # poses per chunk of the host-buffer query
+PC_POSES = SMS * 4 * 128   # the point-cloud baseline's launch: one full wave
 
 
 def query_source_digest(files=("query.cu", "gather.cuh", "fif_common.cuh")):
@@ -160,7 +166,30 @@ def time_events(fn, steps, warmup, stream):
     return [a.elapsed_time(b) for a, b in evs]
 
 
-def fma_probe_tflops(fif, dev, stream, blocks=8 * 152, iters=1 << 14):
+def probe_lib():
+    """The benchmark's FP32 FMA throughput probe (libfif_probe.so, built beside the product
+    library from csrc/probe/; not part of the product ABI):
+    fif_fma_probe(d_sink, blocks, iters, packed, stream) -> status."""
+    import ctypes
+    from paper_2008_03324_gb300 import build as B
+    B.build()
+    L = ctypes.CDLL(B.PROBE_LIB)
+    L.fif_fma_probe.restype = ctypes.c_int32
+    L.fif_fma_probe.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]
+    return L
+
+
+def fma_probe(sink, blocks, iters, packed, stream):
+    """One probe launch: blocks CTAs of 256 threads, 2 * 8 * iters flops per thread, on `stream`."""
+    import ctypes
+    assert sink.is_cuda and sink.dtype.itemsize == 4 and sink.numel() >= blocks * 256
+    rc = probe_lib().fif_fma_probe(ctypes.c_void_p(sink.data_ptr()), int(blocks), int(iters), int(bool(packed)),
+                                   ctypes.c_void_p(stream.cuda_stream))
+    if rc != 0:
+        raise RuntimeError(f"fif_fma_probe: {rc}")
+
+
+def fma_probe_tflops(dev, stream, blocks=8 * 152, iters=1 << 14):
     """Measured FP32 FMA throughput of this GPU (fif_fma_probe: eight independent chains per
     thread, scalar or packed f32x2), best of five launches: context for the nominal peak the
     ALU-bound build is reported against."""
@@ -168,7 +197,7 @@ def fma_probe_tflops(fif, dev, stream, blocks=8 * 152, iters=1 << 14):
     sink = torch.empty(blocks * 256, dtype=torch.float32, device=dev)
     out = {}
     for name, packed in (("scalar", False), ("packed_f32x2", True)):
-        t = time_events(lambda: fif.fma_probe(sink, blocks, iters, packed, stream), 5, 2, stream)
+        t = time_events(lambda: fma_probe(sink, blocks, iters, packed, stream), 5, 2, stream)
         out[name] = 2 * 8 * iters * blocks * 256 / (min(t) * 1e-3) / 1e12
     assert bool(torch.isfinite(sink).all())
     return out
@@ -303,10 +332,14 @@ def gp_block(fif, synth, spec, lm, r_max, m, ns, dev, stream, hbm_peak, build_st
 def method_accuracy(fif, synth, dev, n_poses=200):
     """Accuracy of the field representations against the exact point-cloud FIM (Sec. VII-A,
     Eq. fim_rel_diff): 1000 random landmarks in a 10 x 10 x 5 m box, fields on the 9 x 9 x 4 m
-    region inside it at 0.5 m, poses at random nodes with uniform rotations, e_FIM =
-    ||I_field - I_pc||_F / ||I_pc||_F in the camera frame (the field at its own node isolates the
-    visibility model, as the paper's nearest-voxel test does).  Context for the paper's table,
-    not a parity check."""
+    region inside it at 0.5 m, poses at random nodes with uniform rotations, e = ||I_field -
+    I_pc||_F / ||I_pc||_F in the camera frame (the field at its own node isolates the visibility
+    model, as the paper's nearest-voxel test does).  Three aggregates over the poses that see a
+    landmark: the mean and the median of e, and the ratio of sums sum ||I_field - I_pc|| / sum
+    ||I_pc|| (per-pose e has a heavy tail where a landmark just outside the image sits close to
+    the camera); two exact cameras with the paper's 90-degree horizontal field of view: the
+    library's default 640 x 640 image and a 640 x 480 one.  Context for the paper's table, not a
+    parity check."""
     import torch
     lm = synth.random_box(8, 1000)
     spec = synth.GridSpec((0.5, 0.5, 0.5), 0.5, (19, 19, 9))
@@ -318,8 +351,11 @@ def method_accuracy(fif, synth, dev, n_poses=200):
     P = torch.from_numpy(poses).to(dev)
     L = torch.from_numpy(lm).to(dev)
     prm_pc = fif.make_params(r_min=0.1, r_max=30.0)
-    fim_pc = torch.empty(n_poses, 21, device=dev)
-    fif.pointcloud_fim(L, prm_pc, fif.make_pinhole(), P, 0, fim_pc, None, None, None)
+    cams = {"640x640": fif.make_pinhole(), "640x480": fif.make_pinhole(cy=240.0, height=480)}
+    fim_pc = {}
+    for cname, cam in cams.items():
+        fim_pc[cname] = torch.empty(n_poses, 21, device=dev)
+        fif.pointcloud_fim(L, prm_pc, cam, P, 0, fim_pc[cname], None, None, None)
     w = torch.tensor([1.0 if r == c else 2.0 for r in range(6) for c in range(r, 6)], device=dev)
     fro = lambda x: torch.sqrt((w * x.double() ** 2).sum(1))
     out = {}
@@ -334,11 +370,15 @@ def method_accuracy(fif, synth, dev, n_poses=200):
             fld = fif.Field(spec.origin, spec.res, spec.dims, prm, storage=fif.STORAGE_GP, gp=gp)
         fld.build(L)
         fim, _, _, _ = fld.query(P, fif.Q_NEAREST)
-        ref = fro(fim_pc)
-        seen = (ref > 0).cpu().numpy()          # poses whose camera sees at least one landmark
-        e = (fro(fim - fim_pc) / ref.clamp_min(1e-300)).cpu().numpy()[seen]
-        out[name] = {"mean_pct": float(100 * e.mean()), "median_pct": float(100 * np.median(e)),
-                     "poses": int(seen.sum())}
+        out[name] = {}
+        for cname in cams:
+            ref = fro(fim_pc[cname])
+            seen = (ref > 0).cpu().numpy()          # poses whose camera sees at least one landmark
+            d = fro(fim - fim_pc[cname]).cpu().numpy()[seen]
+            r = ref.cpu().numpy()[seen]
+            e = d / r
+            out[name][cname] = {"mean_pct": float(100 * e.mean()), "median_pct": float(100 * np.median(e)),
+                                "ratio_of_sums_pct": float(100 * d.sum() / r.sum()), "poses": int(seen.sum())}
     out["paper_pct"] = {"Q-I-0.5": 64.26, "Q-I-0.8": 164.92, "G-I-30": 11.15, "G-I-50": 9.88, "G-I-70": 9.49}
     return out
 
@@ -435,7 +475,7 @@ def main():
                      "fma_pipe_active_ncu": (BUILD_PIPE["fma_pipe_active"] if BUILD_PIPE["digest"] ==
                                              query_source_digest(("build.cu", "landmark_stream.cuh", "fif_common.cuh"))
                                              else None),
-                     "fma_probe_tflops": fma_probe_tflops(fif, dev, stream)},
+                     "fma_probe_tflops": fma_probe_tflops(dev, stream)},
     }
     # ---------------- incremental update (Sec. VI-A-1): add then remove 1,000 landmarks ----------------
     delta = torch.from_numpy(synth.random_box(seed=21, n=1000, size=(50.0, 50.0, 10.0))).to(dev)
@@ -505,6 +545,7 @@ def main():
 
     # ---------------- end to end through host buffers ----------------
     h_poses = torch.from_numpy(synth.random_poses(2000 + rank, m, spec.lo, spec.hi)).pin_memory()
+    h_fim = torch.empty(m, 21, dtype=torch.float32).pin_memory()
     h_met = torch.empty(m, 3, dtype=torch.float64).pin_memory()
     h_sg = torch.empty(m, dtype=torch.int8).pin_memory()
     h_st = torch.empty(m, dtype=torch.int32).pin_memory()
@@ -515,7 +556,7 @@ def main():
     staging = torch.empty(fif.query_host_staging_bytes(E2E_CHUNK), dtype=torch.uint8, device=dev)
 
     def e2e_step():
-        fif.query_host(field.c, h_poses, fif.Q_METRICS, None, h_met, h_sg, h_st, chunk=E2E_CHUNK, staging=staging,
+        fif.query_host(field.c, h_poses, fif.Q_METRICS, h_fim, h_met, h_sg, h_st, chunk=E2E_CHUNK, staging=staging,
                        stream=stream, copy_stream=copy_stream)
 
     e2e_steps = max(3, args.steps // 2)
@@ -523,16 +564,32 @@ def main():
     launches += 0
     e2e_ms = dist.max_over_ranks(float(np.mean(te)), dev)
     e2e = {"value": m * ws / (e2e_ms * 1e-3), "unit": "queries/s", "h2d_bytes_per_step": m * 28,
-           "d2h_bytes_per_step": m * (24 + 1 + 4), "ms_per_step": e2e_ms,
-           "api": f"fif_query_host, pinned host buffers, chunks of {E2E_CHUNK} poses"}
+           "d2h_bytes_per_step": m * (84 + 24 + 1 + 4), "ms_per_step": e2e_ms,
+           "api": (f"fif_query_host, pinned host buffers, chunks of {E2E_CHUNK} poses; the same outputs as the "
+                   "timed step (FIM, trace / log|det| / lambda_min, sign, status)")}
     del staging
 
     # ---------------- point-cloud baseline (all 200k landmarks) ----------------
-    mp = 8192
+    # ---------------- the same step at v_alpha = 0.8 (non-negative visibility: PSD FIMs) ----------------
+    f08 = field.with_params(fif.make_params(r_max=r_max, v_alpha=0.8))
+    t08 = time_events(lambda: fif.query(f08.c, poses, fif.Q_METRICS, fim, met, sg, st), 10, 3, stream)
+    ms08 = float(np.mean(t08))
+    st08 = st.cpu().numpy()
+    out["v_alpha_0.8"] = {"queries_per_s": m / (ms08 * 1e-3), "kernel_ms": ms08,
+                          "roofline_frac": m * QUERY_BYTES_PER_POSE / (ms08 * 1e-3) / 1e9 / hbm_peak,
+                          "status_counts": {"outside": int(((st08 & 1) != 0).sum()),
+                                            "not_pd": int(((st08 & 4) != 0).sum())}}
+    del f08
+
+    # one thread per pose, 128-thread CTAs, 4 resident per SM: 152 x 4 CTAs fill the GPU once
+    mp = PC_POSES
     tp = time_events(lambda: fif.pointcloud_fim(lm, params, fif.make_pinhole(), poses[:mp], fif.Q_METRICS,
                                                 fim, met, sg, st), 3, 1, stream)
-    pc_rate = mp / (float(np.mean(tp)) * 1e-3)
+    pc_ms = float(np.mean(tp))
+    pc_rate = mp / (pc_ms * 1e-3)
     out["pointcloud"] = {"queries_per_s": pc_rate, "landmarks": int(lm.shape[0]), "poses": mp,
+                         "launch": f"{mp} poses = {mp // 128} CTAs of 128 threads (4 per SM on 152 SMs)",
+                         "kernel_ms": pc_ms, "pose_landmark_pairs_per_s": mp * int(lm.shape[0]) / (pc_ms * 1e-3),
                          "field_speedup": (value / ws) / pc_rate}
 
     # ---------------- bfloat16 storage (same map, same poses) ----------------
@@ -540,8 +597,9 @@ def main():
     fif.build(field16.c, lm, wsb)
     t16 = time_events(lambda: fif.query(field16.c, poses, fif.Q_METRICS, fim, met, sg, st), 10, 3, stream)
     ms16 = float(np.mean(t16))
-    b16 = 8 * 210 * 2 + 7 * 4 + 21 * 4 + 3 * 8 + 1 + 4
+    b16 = BF16_QUERY_BYTES_PER_POSE
     out["bf16"] = {"queries_per_s": m / (ms16 * 1e-3), "kernel_ms": ms16, "bytes_per_pose": b16,
+                   "io_bytes_per_pose": QUERY_IO_BYTES_PER_POSE,
                    "roofline": {"bound": "hbm", "achieved": m * b16 / (ms16 * 1e-3) / 1e9, "peak": hbm_peak,
                                 "unit": "GB/s", "frac": m * b16 / (ms16 * 1e-3) / 1e9 / hbm_peak}}
     torch.cuda.empty_cache()
@@ -551,11 +609,14 @@ def main():
     ttb = time_events(lambda: fif.build(ftr.c, lm, wsb), 2, 1, stream)
     ttq = time_events(lambda: fif.query(ftr.c, poses, fif.Q_TRACE | fif.Q_WORLD, None, met, None, st), 10, 3,
                       stream)
-    btr = 8 * 10 * 4 + 7 * 4 + 8 + 4
+    btr = TRACE_QUERY_BYTES_PER_POSE
+    tq_ms = float(np.mean(ttq))
     out["trace_field"] = {"field_bytes": ftr.coeffs.numel() * 4, "build_ms": float(np.mean(ttb)),
-                          "queries_per_s": m / (float(np.mean(ttq)) * 1e-3), "bytes_per_pose": btr,
-                          "roofline": {"bound": "hbm", "achieved": m * btr / (float(np.mean(ttq)) * 1e-3) / 1e9,
-                                       "peak": hbm_peak, "unit": "GB/s"}}
+                          "queries_per_s": m / (tq_ms * 1e-3), "bytes_per_pose": btr,
+                          "io_bytes_per_pose": 7 * 4 + 8 + 4, "kernel_ms": tq_ms,
+                          "roofline": {"bound": "hbm", "achieved": m * btr / (tq_ms * 1e-3) / 1e9,
+                                       "peak": hbm_peak, "unit": "GB/s",
+                                       "frac": m * btr / (tq_ms * 1e-3) / 1e9 / hbm_peak}}
     del ftr
 
     # ---------------- GP visibility field (N_s = 70, the paper's choice) ----------------
@@ -667,7 +728,8 @@ def main():
                                      if QUERY_TRAFFIC["digest"] == query_source_digest() else None),
                          "traffic_note": "ncu dram read+write bytes per launch of query_kernel (summary in profiles/)",
                          "peak_kind": f"{peak_kind} (MEASURED_PEAKS hbm_gbs)",
-                         "bytes_per_pose": QUERY_BYTES_PER_POSE, "kernel_ms": kernel_ms},
+                         "bytes_per_pose": QUERY_BYTES_PER_POSE, "io_bytes_per_pose": QUERY_IO_BYTES_PER_POSE,
+                         "kernel_ms": kernel_ms},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,

@@ -390,12 +390,16 @@ FIF_API int32_t fif_field_load(fif_field* field, const char* path, void* d_coeff
  * 0 when no bounded device wait has run out since the last reset.  Synchronises `stream`. */
 FIF_API int32_t fif_device_error(int32_t* out_code, int32_t reset, fif_stream_t stream);
 
-/* FP32 FMA throughput probe (measurement infrastructure for the roofline of the ALU-bound
- * builds, not part of the method): `blocks` CTAs of 256 threads each run `iters` rounds of
- * eight independent single-precision FMA chains (packed != 0: four chains of packed f32x2 FMAs,
- * the same eight lanes of work), 2 * 8 * iters flops per thread, and write one float per thread
- * to d_sink (device, at least blocks * 256 floats).  Time it with events on `stream`. */
-FIF_API int32_t fif_fma_probe(float* d_sink, int64_t blocks, int32_t iters, int32_t packed, fif_stream_t stream);
+/* Limit, in nanoseconds of the GPU's global timer, of every bounded device wait in the kernels
+ * launched after this call by fif_query on FIF_STORAGE_F32 / FIF_STORAGE_BF16 fields (and so
+ * fif_query_host), fif_build, fif_build_update and fif_build_static: a bulk copy's completion, a
+ * hand-over between warps, a slot of the landmark ring.  0 restores the default, 2 s.  A wait that
+ * runs out makes its block record FIF_ETIMEOUT in the device error word (fif_device_error), wait
+ * (at most 0.1 s more) for the copies it has issued, and return, leaving that launch's results
+ * incomplete; the context stays usable.  Process-wide (all devices and threads).  Callers keep the
+ * default; a limit far below the time one copy or hand-over takes forces the failure path, which is
+ * how that path is tested.  Always FIF_OK. */
+FIF_API int32_t fif_set_wait_limit(uint64_t limit_ns);
 
 #ifdef __cplusplus
 }

@@ -398,15 +398,19 @@ __global__ void __launch_bounds__(kThreads + 32, 2) build_kernel(BuildArgs a) {
             TileProducer<kTile> prod;
             for (int it = 0;; ++it) {
                 const int slot = it % kSlots;
-                if (it >= kSlots && !mbar_wait_bounded(&S.empty[slot], (uint32_t)((it / kSlots - 1) & 1))) {
+                if (it >= kSlots && !mbar_wait_bounded(&S.empty[slot], (uint32_t)((it / kSlots - 1) & 1), a.wait_ns)) {
                     set_error(a.err, FIF_ETIMEOUT);
+                    drain_fills<kSlots>(S.full, it - kSlots, it);
                     break;
                 }
                 fence_proxy_async();   // the consumers' reads of the slot precede the new copies
                 const int cnt = prod.fill(S.tile[slot], S.runs, S.nruns, sorted, &S.full[slot]);
                 S.tile_count[slot] = cnt;
                 mbar_arrive(&S.full[slot]);
-                if (cnt == 0) break;   // the end marker; every copy issued is consumed before it
+                if (cnt == 0) {       // the end marker
+                    drain_fills<kSlots>(S.full, it - kSlots + 1, it);
+                    break;
+                }
             }
         }
         return;
@@ -457,7 +461,7 @@ __global__ void __launch_bounds__(kThreads + 32, 2) build_kernel(BuildArgs a) {
     for (int it = 0;; ++it) {
         const int slot = it % kSlots;
         const uint32_t par = (uint32_t)((it / kSlots) & 1);
-        if (__any_sync(0xffffffffu, !mbar_wait_bounded(&S.full[slot], par))) {  // the warp exits together
+        if (__any_sync(0xffffffffu, !mbar_wait_bounded(&S.full[slot], par, a.wait_ns))) {  // the warp exits together
             ok = false;
             if (lane == 0) set_error(a.err, FIF_ETIMEOUT);
             break;

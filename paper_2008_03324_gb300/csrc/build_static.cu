@@ -41,6 +41,8 @@ int scratch_address(void** out) {
 
 extern "C" FIF_API int32_t fif_build_static(fif_field* field, const float* d_landmarks, int64_t n,
                                             fif_stream_t stream) {
+    // offered for the quadratic-visibility and trace fields only; a GP field is refused
+    if (field && field->storage == FIF_STORAGE_GP) return FIF_EINVAL;
     const size_t need = fif_build_workspace_bytes(field, n);
     if (need == 0) return FIF_EINVAL;
     if (need > (size_t)FIF_BUILD_STATIC_SCRATCH_BYTES) return FIF_ERANGE;

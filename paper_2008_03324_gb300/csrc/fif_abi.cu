@@ -1,6 +1,7 @@
 // fif_abi.cu -- the extern "C" entry points declared in include/fif.h: argument checks,
 // launch configuration, field files and the device error word.  No device allocation.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -15,6 +16,9 @@ namespace {
 __device__ int g_device_error = 0;
 
 constexpr int32_t kVersion = 10000;  // 1.0.0
+constexpr uint64_t kDefaultWaitNs = 2000000000ull;   // 2 s
+// limit of every bounded device wait in the kernels launched from now on (fif_set_wait_limit)
+std::atomic<uint64_t> g_wait_ns{kDefaultWaitNs};
 constexpr int kMaxDevices = 64;
 int* g_err_ptr[kMaxDevices] = {nullptr};
 std::mutex g_err_mu;
@@ -111,6 +115,7 @@ fif::QueryArgs query_args(const fif_field* f, const float* poses, int64_t m, int
     a.m = m;
     a.flags = flags;
     a.err = device_error_ptr();
+    a.wait_ns = g_wait_ns.load(std::memory_order_relaxed);
     return a;
 }
 
@@ -250,6 +255,7 @@ static int32_t build_impl(fif_field* field, const float* d_landmarks, int64_t n,
     a.out = field->coeffs;
     a.err = device_error_ptr();
     a.accumulate = accumulate;
+    a.wait_ns = g_wait_ns.load(std::memory_order_relaxed);
     if (field->storage == FIF_STORAGE_GP) {
         const fif_gp& gp = field->gp;
         const fif::GpAuxLayout L = fif::gp_aux_layout(gp.n_samples, fif_gp_row_stride(gp.n_samples));
@@ -577,6 +583,11 @@ int32_t fif_field_load(fif_field* field, const char* path, void* d_coeffs, size_
     }
     std::free(own);
     return result;
+}
+
+int32_t fif_set_wait_limit(uint64_t limit_ns) {
+    g_wait_ns.store(limit_ns == 0 ? kDefaultWaitNs : limit_ns, std::memory_order_relaxed);
+    return FIF_OK;
 }
 
 int32_t fif_device_error(int32_t* out_code, int32_t reset, fif_stream_t stream) {

@@ -26,6 +26,7 @@ struct QueryArgs {
     int8_t* sign;
     int32_t* status;
     int* err;
+    uint64_t wait_ns;          // limit of each bounded device wait (fif_set_wait_limit)
     // GP visibility field (storage FIF_STORAGE_GP)
     int gp_ns, gp_rs;
     const float4* gp_axes;     // [2][ns]: axes as (high, low) single-precision parts (x, y, z, 0)
@@ -89,6 +90,7 @@ struct BuildArgs {
     void* out;
     int* err;
     int accumulate;   // 0: overwrite the field; +1 / -1: add / subtract these landmarks' share
+    uint64_t wait_ns; // limit of each bounded device wait (fif_set_wait_limit)
     // GP visibility field (storage FIF_STORAGE_GP): v^s_g = 1 / (1 + 2^(gp_shift - gp_scale z_g.u))
     const float4* gp_axes;    // [ns] (x, y, z, 0)
     int gp_ns, gp_rs;

@@ -121,15 +121,19 @@ __global__ void __launch_bounds__(kGbThreads + 32, 1) gp_build_kernel(BuildArgs 
             TileProducer<kGbTile> prod;
             for (int it = 0;; ++it) {
                 const int slot = it % kGbSlots;
-                if (it >= kGbSlots && !mbar_wait_bounded(&S.empty[slot], (uint32_t)((it / kGbSlots - 1) & 1))) {
+                if (it >= kGbSlots && !mbar_wait_bounded(&S.empty[slot], (uint32_t)((it / kGbSlots - 1) & 1), a.wait_ns)) {
                     set_error(a.err, FIF_ETIMEOUT);
+                    drain_fills<kGbSlots>(S.full, it - kGbSlots, it);
                     break;
                 }
                 fence_proxy_async();   // the node warps' reads of the slot precede the new copies
                 const int cnt = prod.fill(S.tile[slot], S.runs, S.nruns, sorted, &S.full[slot]);
                 S.tile_count[slot] = cnt;
                 mbar_arrive(&S.full[slot]);
-                if (cnt == 0) break;   // the end marker; every copy issued is consumed before it
+                if (cnt == 0) {       // the end marker
+                    drain_fills<kGbSlots>(S.full, it - kGbSlots + 1, it);
+                    break;
+                }
             }
         }
         return;
@@ -206,7 +210,7 @@ __global__ void __launch_bounds__(kGbThreads + 32, 1) gp_build_kernel(BuildArgs 
     for (int it = 0;; ++it) {
         const int slot = it % kGbSlots;
         const uint32_t par = (uint32_t)((it / kGbSlots) & 1);
-        if (__any_sync(0xffffffffu, !mbar_wait_bounded(&S.full[slot], par))) {   // the warp exits together
+        if (__any_sync(0xffffffffu, !mbar_wait_bounded(&S.full[slot], par, a.wait_ns))) {   // the warp exits together
             ok = false;
             if (lane == 0) set_error(a.err, FIF_ETIMEOUT);
             break;

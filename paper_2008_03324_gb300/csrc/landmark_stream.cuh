@@ -79,6 +79,18 @@ struct TileProducer {
     }
 };
 
+// Wait, with a short bound, until the bulk copies of fills f0 .. f1 - 1 have landed (the "full"
+// phase of a fill completes when its bytes have arrived), so the producer never lets its block
+// exit while a copy still writes the block's shared memory.  Slot f % kSlots must not have been
+// refilled since fill f (its phase parity would then alias): a producer that gave up waiting at
+// iteration it drains it - kSlots .. it - 1; after the end marker of iteration it, it - kSlots + 1
+// .. it - 1.
+template <int kSlots>
+FIF_DEV void drain_fills(uint64_t* full, int f0, int f1, uint64_t limit_ns = 100000000ull) {
+    for (int f = max(0, f0); f < f1; ++f)
+        mbar_wait_bounded(&full[f % kSlots], (uint32_t)((f / kSlots) & 1), limit_ns);
+}
+
 __device__ __forceinline__ void kahan_merge(float* hs, float* ls, int idx, float x) {
     const float s = hs[idx], c = ls[idx];
     const float y = x - c;

@@ -1,10 +1,13 @@
-// fma_probe.cu -- FP32 FMA throughput probe (sm_103a).  Measurement infrastructure for the
-// roofline of the ALU-bound kernels (the field builds), not part of the method: every thread
+// fma_probe.cu -- FP32 FMA throughput probe (sm_103a), built as its own library
+// (libfif_probe.so) for the benchmark and kept out of the product library and its header.
+// Measurement infrastructure for the roofline of the ALU-bound kernels (the field builds), not
+// part of the method: every thread
 // runs `iters` rounds of eight independent FMA chains -- scalar fma.rn.f32, or four chains of
 // packed fma.rn.f32x2 carrying the same eight lanes of work -- unrolled 8 rounds deep so that
 // loop control takes few issue slots and the FMA pipe is the only limit.  Work per launch: 2 * 8 * iters flops per thread (both forms).
-#include "fif_common.cuh"
-#include "fif_internal.h"
+#include <cstdint>
+
+#include "../fif_common.cuh"
 
 namespace fif {
 
@@ -43,11 +46,14 @@ __global__ void __launch_bounds__(kProbeThreads) fma_probe_kernel(float* sink, i
 
 }  // namespace fif
 
-int32_t fif_fma_probe(float* d_sink, int64_t blocks, int32_t iters, int32_t packed, fif_stream_t stream) {
+// d_sink: device float[blocks * 256]; FIF_OK, FIF_EINVAL (bad count or NULL), FIF_EALIGN or FIF_ECUDA
+extern "C" __attribute__((visibility("default"))) int32_t fif_fma_probe(float* d_sink, int64_t blocks,
+                                                                      int32_t iters, int32_t packed,
+                                                                      cudaStream_t stream) {
     if (!d_sink || blocks <= 0 || blocks > (int64_t)INT32_MAX || iters <= 0) return FIF_EINVAL;
     if (reinterpret_cast<uintptr_t>(d_sink) & 3u) return FIF_EALIGN;
     // a = 1 - 2^-20, b = 2^-24: the chains stay finite and bounded for any iteration count
-    fif::fma_probe_kernel<<<(unsigned)blocks, fif::kProbeThreads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+    fif::fma_probe_kernel<<<(unsigned)blocks, fif::kProbeThreads, 0, stream>>>(
         d_sink, iters, packed ? 1 : 0, 1.f - 9.5367431640625e-7f, 5.9604644775390625e-8f);
     return cudaPeekAtLastError() == cudaSuccess ? FIF_OK : FIF_ECUDA;
 }

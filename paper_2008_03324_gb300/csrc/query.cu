@@ -227,7 +227,7 @@ __global__ void __launch_bounds__((NG + NM) * 32, 1) query_kernel(QueryArgs args
         for (int64_t g = (int64_t)blockIdx.x * kGather + warp; g < groups; g += ngather, ++k) {
             const int sl = k & 1;
             const uint32_t use = (uint32_t)(k >> 1);
-            if (__any_sync(0xffffffffu, *abort_flag != 0 || !mbar_wait_bounded(&G.empty[sl], (use & 1u) ^ 1u))) {
+            if (__any_sync(0xffffffffu, *abort_flag != 0 || !mbar_wait_bounded(&G.empty[sl], (use & 1u) ^ 1u, args.wait_ns))) {
                 set_error(args.err, FIF_ETIMEOUT);
                 *abort_flag = 1;
                 break;
@@ -334,7 +334,7 @@ __global__ void __launch_bounds__((NG + NM) * 32, 1) query_kernel(QueryArgs args
                     const int ipf = i + kStages - 1 + kPrefetch;
                     if (ipf < cnt) bulk_prefetch_l2(pair_src(base_of(ipf), lane), L::kPairBytes);
                 }
-                if (__any_sync(0xffffffffu, !mbar_wait_bounded(&G.bars[s], (phase_bits >> s) & 1u))) {
+                if (__any_sync(0xffffffffu, !mbar_wait_bounded(&G.bars[s], (phase_bits >> s) & 1u, args.wait_ns))) {
                     set_error(args.err, FIF_ETIMEOUT);
                     *abort_flag = 1;
                     // the copies of poses i .. i + kStages - 1 may still be in flight
@@ -404,7 +404,7 @@ __global__ void __launch_bounds__((NG + NM) * 32, 1) query_kernel(QueryArgs args
                 GS& G = *reinterpret_cast<GS*>(smem_raw + gw * kGB);
                 const int sl = k & 1;
                 const uint32_t use = (uint32_t)(k >> 1);
-                if (__any_sync(0xffffffffu, *abort_flag != 0 || !mbar_wait_bounded(&G.full[sl], use & 1u))) {
+                if (__any_sync(0xffffffffu, *abort_flag != 0 || !mbar_wait_bounded(&G.full[sl], use & 1u, args.wait_ns))) {
                     set_error(args.err, FIF_ETIMEOUT);
                     *abort_flag = 1;
                     dead = true;

@@ -87,7 +87,6 @@ _SIGS = {
     "fif_build_static": (_I32, [ctypes.POINTER(FieldC), _VP, _I64, _VP]),
     "fif_build_update": (_I32, [ctypes.POINTER(FieldC), _VP, _I64, _I32, _VP, ctypes.c_size_t, _VP]),
     "fif_query": (_I32, [ctypes.POINTER(FieldC), _VP, _I64, _I32, _VP, _VP, _VP, _VP, _VP]),
-    "fif_fma_probe": (_I32, [_VP, _I64, _I32, _I32, _VP]),
     "fif_query_host_staging_bytes": (ctypes.c_size_t, [_I64]),
     "fif_query_host": (_I32, [ctypes.POINTER(FieldC), _VP, _I64, _I32, _VP, _VP, _VP, _VP, _I64, _VP,
                               ctypes.c_size_t, _VP, _VP]),
@@ -97,6 +96,7 @@ _SIGS = {
     "fif_field_save": (_I32, [ctypes.POINTER(FieldC), ctypes.c_char_p, _VP, _VP]),
     "fif_field_load": (_I32, [ctypes.POINTER(FieldC), ctypes.c_char_p, _VP, ctypes.c_size_t, _VP, _VP]),
     "fif_device_error": (_I32, [ctypes.POINTER(_I32), _I32, _VP]),
+    "fif_set_wait_limit": (_I32, [ctypes.c_uint64]),
     "fif_gp_row_stride": (_I32, [_I32]),
     "fif_gp_stride": (_I32, [_I32]),
     "fif_gp_aux_bytes": (ctypes.c_size_t, [_I32]),
@@ -358,14 +358,6 @@ def query(field: FieldC, poses: torch.Tensor, flags=Q_METRICS, fim=None, metrics
                            _ptr(sign), _ptr(status), _stream(stream)), "fif_query")
 
 
-def fma_probe(sink: torch.Tensor, blocks: int, iters: int, packed: bool, stream=None):
-    """fif_fma_probe: FP32 FMA throughput probe (2 * 8 * iters flops per thread, 256 threads per
-    block); sink is a float32 device tensor of at least blocks * 256 elements."""
-    assert sink.is_cuda and sink.dtype == torch.float32 and sink.numel() >= blocks * 256
-    _check(lib().fif_fma_probe(_ptr(sink), int(blocks), int(iters), int(bool(packed)), _stream(stream)),
-           "fif_fma_probe")
-
-
 def query_host_staging_bytes(chunk: int) -> int:
     return int(lib().fif_query_host_staging_bytes(int(chunk)))
 
@@ -412,6 +404,12 @@ def device_error(reset=True, stream=None) -> int:
     v = _I32(0)
     _check(lib().fif_device_error(ctypes.byref(v), int(bool(reset)), _stream(stream)), "fif_device_error")
     return int(v.value)
+
+
+def set_wait_limit(limit_ns: int = 0):
+    """fif_set_wait_limit: limit of every bounded device wait of the kernels launched afterwards
+    (0 restores the default of 2 s)."""
+    _check(lib().fif_set_wait_limit(int(limit_ns)), "fif_set_wait_limit")
 
 
 # ---------------------------------------------------------------------------

@@ -42,6 +42,26 @@ def rel_fro(A, B):
     return fro(np.asarray(A) - np.asarray(B)) / np.maximum(fro(B), 1e-300)
 
 
+U32 = 2.0 ** -24   # unit roundoff of single precision
+BLOCK_FLOOR = 16 * U32   # absolute floor of the per-block check, relative to the node's norm
+
+
+def block_ratio(got, ref, tau, floor=BLOCK_FLOOR):
+    """Per node and monomial block k of fields [N, 10, 6, 6] (float64):
+    ||got_k - ref_k||_F / max(tau ||ref_k||_F, floor ||ref||_F), where ||ref||_F is the node's norm
+    over all 10 blocks.  A block passes at <= 1: within tau of its own norm, or, for a block far
+    smaller than its node, within a few single-precision roundings of the node's moments (every
+    stored coefficient is a short integer combination of moment sums bounded by the node's
+    norm).  A block that is wrong by 1 % at 1e-3 of the node's norm fails."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    d = fro(got - ref)                          # [N, 10]
+    rk = fro(ref)                               # [N, 10]
+    node = np.sqrt((rk ** 2).sum(axis=1, keepdims=True))
+    den = np.maximum(tau * rk, floor * node)
+    return np.where(den > 0, d / np.where(den > 0, den, 1.0), np.where(d > 0, np.inf, 0.0))
+
+
 def pack_field(F_local, stride=216):
     """Oracle node-local coefficients [N, 10, 6, 6] -> library layout [N, stride] float32."""
     N = F_local.shape[0]
@@ -108,10 +128,12 @@ def round_bf16(x):
     return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-def local_to_world(F_local, spec):
-    """Node-local coefficients [N, 10, 6, 6] -> the paper's world frame, C^w = M_c^T C M_c (FP64)."""
+def local_to_world(F_local, spec, nodes=None):
+    """Node-local coefficients [N, 10, 6, 6] -> the paper's world frame, C^w = M_c^T C M_c (FP64);
+    row n belongs to lattice node nodes[n] (default: node n)."""
+    F_local = np.asarray(F_local, dtype=np.float64)
     N = F_local.shape[0]
-    idx = np.arange(N)
+    idx = np.arange(N) if nodes is None else np.asarray(nodes, dtype=np.int64).reshape(-1)
     nx, ny = spec.dims[0], spec.dims[1]
     c = np.stack([spec.origin[0] + spec.res * (idx % nx), spec.origin[1] + spec.res * ((idx // nx) % ny),
                   spec.origin[2] + spec.res * (idx // (nx * ny))], axis=1)
@@ -138,3 +160,36 @@ def build_c_client(out_dir):
            f"-Wl,-rpath,{os.path.join(cuda, 'lib64')}", "-lm"]
     subprocess.run(cmd, check=True, capture_output=True, text=True)
     return exe
+
+
+class OracleNodes:
+    """Coefficient sets of lattice nodes built by the FP64 oracle on demand and cached: for test
+    workloads whose lattice is too large to build whole (every node costs a pass over all
+    landmarks), only the nodes that the poses under test touch."""
+
+    def __init__(self, landmarks, spec, params):
+        self.landmarks = landmarks
+        self.spec = spec
+        self.grid = oracle_grid(spec)
+        self.params = params
+        self.cache = {}
+
+    def local(self, nodes):
+        """[len(nodes), 10, 6, 6] node-local (about the node) coefficients."""
+        nodes = np.asarray(nodes, dtype=np.int64).reshape(-1)
+        missing = np.unique(nodes[[n not in self.cache for n in nodes.tolist()]])
+        if missing.size:
+            blocks = O.field_nodes(self.landmarks, self.grid, self.params, missing, about_node=True)
+            for n, b in zip(missing.tolist(), blocks):
+                self.cache[n] = b
+        return np.stack([self.cache[n] for n in nodes.tolist()]) if nodes.size else np.zeros((0, 10, 6, 6))
+
+    def world(self, nodes):
+        nodes = np.asarray(nodes, dtype=np.int64)
+        W = local_to_world(self.local(nodes), self.spec, nodes.reshape(-1))
+        return W.reshape(nodes.shape + (10, 6, 6))
+
+    def corners(self, poses):
+        """(corners [m, 8, 10, 6, 6] world frame, w, dw, nodes) of the trilinear query cells."""
+        nodes, w, dw, _ = O.query_cells(self.grid, poses)
+        return self.world(nodes), w, dw, nodes

@@ -102,10 +102,6 @@ def test_calls_reject_bad_arguments_before_any_launch(F):
     assert lib.fif_pointcloud_fim(fake, 5, ctypes.byref(p), ctypes.byref(cam), fake, 5, F.Q_METRICS,
                                   None, fake, None, None, None) == F.EINVAL
     assert lib.fif_device_error(None, 0, None) == F.EINVAL
-    assert lib.fif_fma_probe(None, 4, 10, 0, None) == F.EINVAL
-    assert lib.fif_fma_probe(fake, 0, 10, 0, None) == F.EINVAL
-    assert lib.fif_fma_probe(fake, 4, 0, 1, None) == F.EINVAL
-    assert lib.fif_fma_probe(ctypes.c_void_p(0x100002), 4, 10, 0, None) == F.EALIGN
     assert lib.fif_field_load(None, b"/nonexistent", fake, 16, None, None) == F.EINVAL
     f2 = F.FieldC()
     assert lib.fif_field_load(ctypes.byref(f2), b"/nonexistent/x.fif", fake, 16, None, None) == F.EIO
@@ -159,3 +155,23 @@ def test_field_load_rejects_bad_files_before_any_copy(F, tmp_path):
         assert lib.fif_field_load(ctypes.byref(f), str(p).encode(), fake, 1 << 20, None, None) == F.EFORMAT, name
     assert lib.fif_field_load(ctypes.byref(f), str(tmp_path / "none.fif").encode(), fake, 1 << 20, None,
                               None) == F.EIO
+
+
+def test_fma_probe_is_outside_the_product_library(F):
+    """The FP32 FMA throughput probe lives in the benchmark's own libfif_probe.so: the product
+    library does not export it, and the probe's argument checks return before any launch."""
+    import bench
+    assert not hasattr(F.lib(), "fif_fma_probe")
+    P = bench.probe_lib()
+    fake = ctypes.c_void_p(0x100000)
+    assert P.fif_fma_probe(None, 4, 10, 0, None) == F.EINVAL
+    assert P.fif_fma_probe(fake, 0, 10, 0, None) == F.EINVAL
+    assert P.fif_fma_probe(fake, 4, 0, 1, None) == F.EINVAL
+    assert P.fif_fma_probe(ctypes.c_void_p(0x100002), 4, 10, 0, None) == F.EALIGN
+
+
+def test_wait_limit_setter(F):
+    """fif_set_wait_limit accepts any limit (0 restores the default) and needs no GPU."""
+    lib = F.lib()
+    assert lib.fif_set_wait_limit(1000) == F.OK
+    assert lib.fif_set_wait_limit(0) == F.OK

@@ -39,6 +39,8 @@ def test_room_build_all_nodes(F):
     ref = X.room_field_oracle(True)
     err = X.rel_fro(got.reshape(-1, 10 * 6, 6), ref.reshape(-1, 10 * 6, 6))
     assert err.max() <= X.TAU_F32, err.max()
+    blk = X.block_ratio(got, ref, X.TAU_F32)
+    assert blk.max() <= 1.0, (blk.max(), np.unravel_index(blk.argmax(), blk.shape))
     assert np.all(field.coeffs.cpu().numpy()[:, 210:] == 0)
     # the in-shell pair count is an integer decision taken identically on both sides
     grid = X.oracle_grid(X.ROOM["grid"])
@@ -57,6 +59,8 @@ def test_warehouse_build_sampled_nodes(F):
     got = X.unpack_field(field.coeffs[torch.from_numpy(nodes).cuda()].cpu().numpy())
     err = X.rel_fro(got.reshape(-1, 60, 6), ref.reshape(-1, 60, 6))
     assert err.max() <= X.TAU_F32, (err.max(), nodes[err.argmax()])
+    blk = X.block_ratio(got, ref, X.TAU_F32)
+    assert blk.max() <= 1.0, (blk.max(), np.unravel_index(blk.argmax(), blk.shape))
     inshell, cand, dropped = F.build_stats(ws, field, len(sc.landmarks))
     assert 0 < inshell <= cand and dropped == 0
 
@@ -70,6 +74,7 @@ def test_ragged_lattice(F, dims):
     ref = O.full_field(lm, X.oracle_grid(spec), O.make_params(r_max=4.0), about_node=True)
     got = X.unpack_field(field.coeffs.cpu().numpy())
     assert X.rel_fro(got.reshape(-1, 60, 6), ref.reshape(-1, 60, 6)).max() <= X.TAU_F32
+    assert X.block_ratio(got, ref, X.TAU_F32).max() <= 1.0
 
 
 def test_empty_map_and_far_landmarks(F):
@@ -99,6 +104,8 @@ def test_bf16_storage(F):
     got = X.unpack_field(field.coeffs.float().cpu().numpy())
     ref = X.room_field_oracle(True)
     assert X.rel_fro(got.reshape(-1, 60, 6), ref.reshape(-1, 60, 6)).max() <= X.TAU_BF16
+    # each entry is rounded to bfloat16 on its own, so every block keeps the relative bound
+    assert X.block_ratio(got, ref, X.TAU_BF16).max() <= 1.0
 
 
 def test_end_to_end_warehouse_build_and_query(F):

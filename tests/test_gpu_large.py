@@ -41,6 +41,7 @@ def test_large_map_build_and_query(F, scene):
     got = X.unpack_field(field.coeffs[torch.from_numpy(nodes).cuda()].cpu().numpy())
     nz = X.fro(ref.reshape(-1, 60, 6)) > 0
     assert X.rel_fro(got.reshape(-1, 60, 6)[nz], ref.reshape(-1, 60, 6)[nz]).max() <= X.TAU_F32
+    assert X.block_ratio(got[nz], ref[nz], X.TAU_F32).max() <= 1.0
     inshell, cand, dropped = F.build_stats(ws, field, lm.shape[0])
     assert dropped == 0 and inshell > 1e11
     # end to end query of 150 poses in the building
@@ -57,3 +58,4 @@ def test_large_map_build_and_query(F, scene):
     got16 = X.unpack_field(f16.coeffs[torch.from_numpy(nodes[:200]).cuda()].float().cpu().numpy())
     nz16 = nz[:200]
     assert X.rel_fro(got16.reshape(-1, 60, 6)[nz16], ref[:200].reshape(-1, 60, 6)[nz16]).max() <= X.TAU_BF16
+    assert X.block_ratio(got16[nz16], ref[:200][nz16], X.TAU_BF16).max() <= 1.0

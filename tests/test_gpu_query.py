@@ -227,15 +227,18 @@ def test_query_host_matches_device(F, storage):
 
 
 def test_fma_probe_runs(F):
-    """The FP32 FMA throughput probe (measurement infrastructure) runs in both forms and leaves
-    finite values; bad arguments are rejected."""
+    """The benchmark's FP32 FMA throughput probe (measurement infrastructure, its own library)
+    runs in both forms and leaves finite values; bad arguments are rejected."""
+    import bench
     sink = torch.full((4 * 256,), float("nan"), device="cuda")
+    stream = torch.cuda.current_stream()
     for packed in (False, True):
-        F.fma_probe(sink, 4, 1000, packed)
+        bench.fma_probe(sink, 4, 1000, packed, stream)
         torch.cuda.synchronize()
         assert bool(torch.isfinite(sink).all())
-    assert F.lib().fif_fma_probe(None, 4, 10, 0, None) == F.EINVAL
-    assert F.lib().fif_fma_probe(sink.data_ptr(), 4, 0, 0, None) == F.EINVAL
+    P = bench.probe_lib()
+    assert P.fif_fma_probe(None, 4, 10, 0, None) == F.EINVAL
+    assert P.fif_fma_probe(sink.data_ptr(), 4, 0, 0, None) == F.EINVAL
 
 
 def test_c_client_runs(F, tmp_path):

@@ -31,7 +31,6 @@ def test_static_scratch_build_matches_workspace_build_twice(F):
     ref = F.Field(spec.origin, spec.res, spec.dims, prm)
     ref.build(lm)                         # existing entry point, caller-owned workspace
     torch.cuda.synchronize()
-    ref_np = X.unpack_field(ref.coeffs.cpu().numpy()).reshape(-1, 60, 6)
     lib = F.lib()
     for _ in range(2):                    # the shared scratch keeps the previous call's contents
         out = F.Field(spec.origin, spec.res, spec.dims, prm)
@@ -40,8 +39,11 @@ def test_static_scratch_build_matches_workspace_build_twice(F):
         rc = lib.fif_build_static(ctypes.byref(out.c), ctypes.c_void_p(lm.data_ptr()), lm.shape[0], stream)
         assert rc == F.OK, F.status_str(rc)
         torch.cuda.synchronize()
+        # the same kernels in the same order: bitwise the field of the workspace build, so no
+        # contents of the previous call's scratch can leak into this one
+        assert torch.equal(out.coeffs, ref.coeffs)
         got = X.unpack_field(out.coeffs.cpu().numpy()).reshape(-1, 60, 6)
-        assert X.rel_fro(got, ref_np).max() <= X.TAU_F32
+        assert X.rel_fro(got, X.room_field_oracle(True).reshape(-1, 60, 6)).max() <= X.TAU_F32
         assert np.all(out.coeffs.cpu().numpy()[:, 210:] == 0)
     assert F.device_error() == 0
 
@@ -58,3 +60,18 @@ def test_static_scratch_refuses_oversized_request(F):
     assert rc == F.ERANGE
     torch.cuda.synchronize()
     assert torch.all(fld.coeffs == 3.0)   # nothing was launched
+
+
+def test_static_scratch_refuses_gp_field(F):
+    """A GP-visibility field is refused with FIF_EINVAL before anything runs."""
+    from paper_2008_03324_gb300 import synth
+    spec = X.ROOM["grid"]
+    gp = F.GPModel(synth.fibonacci_sphere(30), 0.89754)
+    fld = F.Field(spec.origin, spec.res, spec.dims, F.make_params(r_max=8.0), storage=F.STORAGE_GP, gp=gp)
+    fld.coeffs.fill_(5.0)
+    lm = torch.from_numpy(X.room_scene().landmarks).cuda()
+    rc = F.lib().fif_build_static(ctypes.byref(fld.c), ctypes.c_void_p(lm.data_ptr()), lm.shape[0],
+                                  ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == F.EINVAL
+    torch.cuda.synchronize()
+    assert torch.all(fld.coeffs == 5.0)
