@@ -17,7 +17,8 @@ during the timed region.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 N > 1 runs under torchrun, one process per GPU, each rank holding a replica of the field and
-answering its own 2^22 poses (weak scaling, no exchange on the data path).
+answering its own 2^22 poses (weak scaling, no exchange on the data path); the field is also
+built as z-slabs, one per rank, gathered into every replica by broadcasts (reported apart).
 """
 from __future__ import annotations
 
@@ -47,7 +48,8 @@ QUERY_BYTES_PER_POSE = 8 * 210 * 4
 QUERY_IO_BYTES_PER_POSE = 7 * 4 + 21 * 4 + 3 * 8 + 1 + 4    # pose in; FIM, metrics, sign, status out
 BF16_QUERY_BYTES_PER_POSE = 8 * 210 * 2
 TRACE_QUERY_BYTES_PER_POSE = 8 * 10 * 4
-BUILD_FLOPS_PER_PAIR = 151   # shell test 8, rsqrt 1, bearing 4, monomials 31, 66 accumulations 107
+# shell test 8, rsqrt 1, bearing and 1/n^2 4, products 26, 66 accumulations (46 FMA, 20 FADD) 112
+BUILD_FLOPS_PER_PAIR = 151
 # DRAM traffic of one query launch per pose, from one ncu capture of query_kernel on the bench's
 # 2^22-pose step (read 29.017 GB + write 0.475 GB for 4,194,304 poses; summary under profiles/),
 # valid while the kernel sources hash to the recorded digest
@@ -310,6 +312,9 @@ def gp_block(fif, synth, spec, lm, r_max, m, ns, dev, stream, hbm_peak, build_st
     st = torch.empty(m, dtype=torch.int32, device=dev)
     tq = time_events(lambda: fif.query(fgp.c, poses, fif.Q_METRICS, None, met, sg, st), query_steps, 3, stream)
     tq_ms = float(np.mean(tq))
+    tc = time_events(lambda: fif.query(fgp.c, poses, fif.Q_METRICS | fif.Q_GP_COMPENSATED, None, met, sg, st),
+                     max(3, query_steps // 2), 2, stream)
+    tc_ms = float(np.mean(tc))
     bpp = 8 * fif.gp_stride(ns) * 4 + 7 * 4 + 3 * 8 + 1 + 4
     ach = m * bpp / (tq_ms * 1e-3) / 1e9
     assert fif.device_error() == 0
@@ -323,7 +328,10 @@ def gp_block(fif, synth, spec, lm, r_max, m, ns, dev, stream, hbm_peak, build_st
                               "frac": ach / hbm_peak,
                               "traffic": (GP_QUERY_TRAFFIC["bytes_per_pose"] * m
                                           if ns == GP_QUERY_TRAFFIC["n_samples"] and GP_QUERY_TRAFFIC["digest"] ==
-                                          query_source_digest(("gp_query.cu", "fif_common.cuh")) else None)}}
+                                          query_source_digest(("gp_query.cu", "fif_common.cuh")) else None)},
+           "compensated_contraction": {"queries_per_s": m / (tc_ms * 1e-3), "query_kernel_ms": tc_ms,
+                                       "frac": m * bpp / (tc_ms * 1e-3) / 1e9 / hbm_peak,
+                                       "flag": "FIF_Q_GP_COMPENSATED (Dot2 contraction, error within 2 u kappa)"}}
     del fgp, ws, poses
     torch.cuda.empty_cache()
     return out
@@ -477,6 +485,37 @@ def main():
                                              else None),
                      "fma_probe_tflops": fma_probe_tflops(dev, stream)},
     }
+    # ---------------- slab-partitioned build on N GPUs (Sec. VI-A-1: the nodes are independent) ----------------
+    # each rank builds its z-slab from the landmarks in the slab's band; one broadcast per rank then
+    # completes every replica (the replica built above is overwritten by the gathered slabs)
+    if ws > 1:
+        ranges = dist.slab_ranges(spec.dims[2], ws)
+        k0, k1 = ranges[rank]
+        nxy = spec.dims[0] * spec.dims[1]
+        if k1 > k0:
+            sub_np = dist.slab_landmarks(scene.landmarks, fif.slab_landmark_band(field.c, k0, k1))
+        else:
+            sub_np = scene.landmarks[:0]
+        sub = torch.from_numpy(np.ascontiguousarray(sub_np)).to(dev)
+        wss = torch.empty(fif.build_workspace_bytes(field.c, max(1, sub.shape[0])), dtype=torch.uint8, device=dev)
+        ts = time_events(lambda: fif.build_slab(field.c, k0, k1, sub, wss) if k1 > k0 else None, build_steps, 1,
+                         stream)
+        ins_slab = fif.build_stats(wss, field, sub.shape[0])[0] if k1 > k0 else 0
+        field.coeffs[: k0 * nxy].zero_()
+        field.coeffs[k1 * nxy:].zero_()
+        dist.barrier()
+        tg = time_events(lambda: dist.gather_slabs(field.coeffs, ranges, nxy), 1, 0, stream)
+        slab_ms = dist.max_over_ranks(float(np.mean(ts)), dev)
+        gather_ms = dist.max_over_ranks(float(tg[0]), dev)
+        ins_all = dist.sum_over_ranks(float(ins_slab), dev)
+        out["build_sharded"] = {
+            "ranks": ws, "slabs": ranges, "landmarks_this_rank": int(sub.shape[0]), "slab_ms_max": slab_ms,
+            "gather_ms": gather_ms, "in_shell_pairs": ins_all, "pairs_per_s": ins_all / (slab_ms * 1e-3),
+            "ms_total": slab_ms + gather_ms,
+            "note": "z-slabs cut at multiples of the 4-layer brick; each slab from its landmark band; the "
+                    "gathered field equals the one-GPU build bitwise (tested)"}
+        del wss, sub
+
     # ---------------- incremental update (Sec. VI-A-1): add then remove 1,000 landmarks ----------------
     delta = torch.from_numpy(synth.random_box(seed=21, n=1000, size=(50.0, 50.0, 10.0))).to(dev)
     wsu = torch.empty(fif.build_workspace_bytes(field.c, delta.shape[0]), dtype=torch.uint8, device=dev)

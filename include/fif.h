@@ -83,6 +83,7 @@ typedef struct CUstream_st* fif_stream_t;
 #define FIF_Q_NEAREST 0x1    /* nearest node only (the paper's "FIM from nearest voxel")  */
 #define FIF_Q_CAMERA 0x0     /* FIM in the camera frame, local perturbation (default)     */
 #define FIF_Q_WORLD 0x2      /* FIM in the world frame, global perturbation about origin  */
+#define FIF_Q_GP_COMPENSATED 0x4 /* GP field only: compensated contraction (see fif_query)   */
 #define FIF_Q_TRACE 0x10     /* compute trace            (metrics column 0)               */
 #define FIF_Q_LOGDET 0x20    /* compute log|det| + sign  (metrics column 1, d_sign)       */
 #define FIF_Q_LMIN 0x40      /* compute lambda_min       (metrics column 2)               */
@@ -252,6 +253,23 @@ FIF_API int32_t fif_build(fif_field* field, const float* d_landmarks, int64_t n,
 FIF_API int32_t fif_build_update(fif_field* field, const float* d_landmarks, int64_t n, int32_t sign,
                                  void* d_workspace, size_t workspace_bytes, fif_stream_t stream);
 
+/* Build only the nodes of one z-slab of the lattice, k_begin <= k < k_end (0 <= k_begin < k_end <=
+ * nz).  Sec. VI-A-1: each node's factor is a sum over the landmarks in its own range shell and
+ * depends on no other node, so the lattice splits into slabs that separate GPUs build apart (one
+ * replica each then gathers the slabs).  Nodes outside the slab are not touched.  Every slab node
+ * gets bitwise the coefficients fif_build gives it from the same landmark array; for the quadratic
+ * and trace fields also from any sub-array, in the same relative order, that keeps every landmark
+ * whose z lies in the band of fif_slab_landmark_band (a GP field only to rounding then).  Workspace
+ * as for fif_build with n landmarks. */
+FIF_API int32_t fif_build_slab(fif_field* field, int32_t k_begin, int32_t k_end, const float* d_landmarks,
+                               int64_t n, void* d_workspace, size_t workspace_bytes, fif_stream_t stream);
+
+/* The band z_lo <= z <= z_hi (world z, as float32) holding every landmark that the build of slab
+ * [k_begin, k_end) can use: the node layers of the slab's bricks widened by the build's cull radius
+ * (r_max + 0.01 + 1e-4 r_max) and a rounding margin.  Host only; FIF_EINVAL on a bad range. */
+FIF_API int32_t fif_slab_landmark_band(const fif_field* field, int32_t k_begin, int32_t k_end, float* z_lo,
+                                       float* z_hi);
+
 /* Size of the fixed device scratch array that fif_build_static uses (16 MiB). */
 #define FIF_BUILD_STATIC_SCRATCH_BYTES (16u << 20)
 
@@ -289,7 +307,12 @@ FIF_API int32_t fif_build_static(fif_field* field, const float* d_landmarks, int
  * (every pointer may then be NULL).
  * GP field (FIF_STORAGE_GP): I(T) = sum_g a_g(z) D_g(t) with the kriging weights
  *   a(z) = (K^s + noise_var I)^-1 K_z^T (K_z in double precision, the product as compensated
- *   single-precision sums with W split into high and low parts), D_g interpolated as above. */
+ *   single-precision sums with W split into high and low parts), D_g interpolated as above.
+ *   The weights change sign and cancel, so the single-precision contraction sum_g a_g D_g loses
+ *   digits in proportion to kappa = sum_g |a_g| ||D_g|| / ||I|| (at most about 16 u kappa relative,
+ *   u = 2^-24); with FIF_Q_GP_COMPENSATED it is a compensated dot product (Dot2) and the query's
+ *   error stays within about 2 u kappa (the storage and weight roundings), at roughly half the
+ *   throughput.  The flag is FIF_EINVAL for other storage. */
 FIF_API int32_t fif_query(const fif_field* field, const float* d_poses, int64_t m, int32_t flags,
                   float* d_fim, double* d_metrics, int8_t* d_sign, int32_t* d_status,
                   fif_stream_t stream);

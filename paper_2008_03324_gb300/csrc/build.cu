@@ -14,15 +14,21 @@
 //  build      one CTA = a brick of 8 x 4 x 4 nodes, one thread = one register-resident
 //             node.  A fifth warp streams the brick's candidate landmarks through a 3-slot
 //             ring of shared-memory tiles with bulk copies (cp.async.bulk + full/empty
-//             mbarriers); the 128 node threads read each landmark as a shared-memory broadcast.
+//             mbarriers); each node warp copies the landmarks near its 4 x 4 x 2 sub-brick into
+//             its own list and its 32 node threads read each as a shared-memory broadcast.
 //
 // Arithmetic per (node, landmark): every entry of v_p[k] * I_i is a polynomial in u of
 // degree <= 4 times 1/n^2, 1/n or 1.  Because |u| = 1, multiplying by (u.u)^m raises any
 // term to degree 3 or 4 (2 or 3 for 1/n), so all 210 entries are fixed integer combinations
 // of 66 moments
 //   sum u^a / n^2 (|a| = 4, 3),  sum u^a / n (|a| = 3, 2),  sum u^a (|a| = 4, 3),
-// and the hot loop accumulates only those 66 (31 monomials + 66 FMA/FADD per pair).
-// Accumulation is compensated: a block of 64 pairs (carried across tiles) is summed in
+// and the hot loop accumulates only those 66.  Its arithmetic runs on packed f32x2 pairs whose
+// halves are the same monomial with x and y exchanged ((x^3, y^3), (x^2 z, y^2 z), ...), so every
+// packed operand comes out of an earlier packed result without register moves; the landmarks sit
+// in shared memory as (x, y, z, z) to give (z, z) the same way.  The degree-4 moments are formed
+// inside their accumulating FMA (a degree-3 monomial times one coordinate), so a pair costs 26
+// products and 66 accumulations (46 FMA, 20 FADD) after the shell test and the bearing.
+// Accumulation is compensated: a block of 128 pairs (carried across tiles) is summed in
 // registers, then the block sum is added to a Kahan (sum, compensation) pair held in shared
 // memory.  The epilogue expands the 66 moments into the 210 stored coefficients through the
 // integer map above, enumerated at compile time.
@@ -38,21 +44,21 @@ namespace fif {
 
 namespace {
 
-constexpr int kBX = 8, kBY = 4, kBZ = 4;
+constexpr int kBX = 8, kBY = 4, kBZ = kBuildBrickZ;
 constexpr int kThreads = kBX * kBY * kBZ;  // 128
 constexpr int kTile = 256;                  // landmarks per tile
 constexpr int kSlots = 3;
-constexpr int kBlock = 64;                  // pairs per register block (Kahan granularity)
-constexpr int kMaxRuns = 2048;
+constexpr int kBlock = 128;                 // pairs per register block (Kahan granularity)
+constexpr int kMaxRuns = 1536;
 constexpr int kMom = 66;
 
-// monomial exponent tables (order fixed by the hot loop)
-constexpr int8_t kMon2[6][3] = {{2, 0, 0}, {0, 2, 0}, {0, 0, 2}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1}};
-constexpr int8_t kMon3[10][3] = {{3, 0, 0}, {0, 3, 0}, {0, 0, 3}, {2, 1, 0}, {2, 0, 1},
-                                               {1, 2, 0}, {0, 2, 1}, {1, 0, 2}, {0, 1, 2}, {1, 1, 1}};
-constexpr int8_t kMon4[15][3] = {{4, 0, 0}, {0, 4, 0}, {0, 0, 4}, {3, 1, 0}, {3, 0, 1},
-                                               {1, 3, 0}, {0, 3, 1}, {1, 0, 3}, {0, 1, 3}, {2, 2, 0},
-                                               {2, 0, 2}, {0, 2, 2}, {2, 1, 1}, {1, 2, 1}, {1, 1, 2}};
+// monomial exponent tables (order fixed by the hot loop: x/y-exchanged pairs, then the rest)
+constexpr int8_t kMon2[6][3] = {{2, 0, 0}, {0, 2, 0}, {1, 0, 1}, {0, 1, 1}, {0, 0, 2}, {1, 1, 0}};
+constexpr int8_t kMon3[10][3] = {{3, 0, 0}, {0, 3, 0}, {2, 0, 1}, {0, 2, 1}, {1, 0, 2}, {0, 1, 2}, {0, 0, 3},
+                                 {2, 1, 0}, {1, 2, 0}, {1, 1, 1}};
+constexpr int8_t kMon4[15][3] = {{4, 0, 0}, {0, 4, 0}, {3, 0, 1}, {0, 3, 1}, {2, 0, 2}, {0, 2, 2}, {1, 0, 3},
+                                 {0, 1, 3}, {0, 0, 4}, {3, 1, 0}, {1, 3, 0}, {2, 2, 0}, {2, 1, 1}, {1, 2, 1},
+                                 {1, 1, 2}};
 // v_p monomials of Eq. quad_vis_component
 constexpr int8_t kVp[10][3] = {{2, 0, 0}, {0, 2, 0}, {0, 0, 2}, {1, 1, 0}, {1, 0, 1},
                                              {0, 1, 1}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {0, 0, 0}};
@@ -149,6 +155,7 @@ __global__ void bin_sort_kernel(float4* __restrict__ sorted, const int* __restri
             }
             sorted[j + 1] = v;
         }
+        for (int i = s; i < e; ++i) sorted[i].w = sorted[i].z;   // (x, y, z, z): packed (z, z) loads
     }
 }
 
@@ -161,7 +168,7 @@ struct BuildSmem {
     float4 tile[kSlots][kTile];
     int2 runs[kMaxRuns];
     int tile_count[kSlots];
-    uint16_t keep[kThreads / 32][kTile];   // per-warp list of the tile's landmarks near its sub-brick
+    float4 keep[kThreads / 32][kTile];   // per-warp copies of the tile's landmarks near its sub-brick
     int nruns;
     uint64_t full[kSlots];    // tile landed (producer arrival + copy bytes)
     uint64_t empty[kSlots];   // every consumer warp is done with the tile
@@ -345,7 +352,8 @@ __global__ void __launch_bounds__(kThreads + 32, 2) build_kernel(BuildArgs a) {
 
     // brick of nodes
     const int nbx = (a.nx + kBX - 1) / kBX, nby = (a.ny + kBY - 1) / kBY;
-    const int brick = blockIdx.x;
+    // the launch covers the z-bricks that meet the slab [k_begin, k_end)
+    const int brick = blockIdx.x + (a.k_begin / kBZ) * nbx * nby;
     const int bxi = brick % nbx, byi = (brick / nbx) % nby, bzi = brick / (nbx * nby);
     const int i0 = bxi * kBX, j0 = byi * kBY, k0 = bzi * kBZ;
     // consumer warp w < 4 owns the 4 x 4 x 2 sub-brick at x offset 4 (w & 1), z offset 2 (w >> 1);
@@ -354,7 +362,9 @@ __global__ void __launch_bounds__(kThreads + 32, 2) build_kernel(BuildArgs a) {
     const bool producer = warp == kThreads / 32;
     const int ti = 4 * (warp & 1) + (lane & 3), tj = (lane >> 2) & 3, tk = 2 * (warp >> 1) + (lane >> 4);
     const int ni = i0 + ti, nj = j0 + tj, nk = k0 + tk;
-    const bool valid = !producer && ni < a.nx && nj < a.ny && nk < a.nz;
+    // nodes of the brick outside the slab run along (their warp's culling box is the full
+    // build's, so every node in the slab sees exactly the full build's arithmetic) but write nothing
+    const bool valid = !producer && ni < a.nx && nj < a.ny && nk < a.nz && nk >= a.k_begin && nk < a.k_end;
     const float cx = __fadd_rn(a.ox, __fmul_rn(a.res, (float)ni));
     const float cy = __fadd_rn(a.oy, __fmul_rn(a.res, (float)nj));
     const float cz = __fadd_rn(a.oz, __fmul_rn(a.res, (float)nk));
@@ -418,40 +428,43 @@ __global__ void __launch_bounds__(kThreads + 32, 2) build_kernel(BuildArgs a) {
 
     // ---- consume ----
     const float rmin2 = a.rmin2, rmax2 = a.rmax2;
-    // register block of the 66 moment sums, in packed pairs following the moment order:
-    // S4n2 (15) = 7 pairs + 1, S3n2 (10) = 5, S3n1 (10) = 5, S2n1 (6) = 3, S4n0 (15) = 7 + 1,
-    // S3n0 (10) = 5
-    float2 a4n2[7], a3n2[5], a3n1[5], a2n1[3], a4n0[7], a3n0[5];
-    float a4n2_14, a4n0_14;
+    const float2 cxy = make_float2(cx, cy), czz = make_float2(cz, cz);
+    // register block of the 66 moment sums in the moment order of the tables above: per group the
+    // packed pairs (x-half, y-half of a monomial pair) first, then the single moments
+    float2 p4n2[4], p3n2[3], p3n1[3], p2n1[2], p4n0[4], p3n0[3];
+    float s4n2[7], s3n2[4], s3n1[4], s2n1[2], s4n0[7], s3n0[4];
     auto zero_block = [&]() {
 #pragma unroll
-        for (int i = 0; i < 7; ++i) a4n2[i] = a4n0[i] = make_float2(0.f, 0.f);
+        for (int i = 0; i < 4; ++i) p4n2[i] = p4n0[i] = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int i = 0; i < 5; ++i) a3n2[i] = a3n1[i] = a3n0[i] = make_float2(0.f, 0.f);
+        for (int i = 0; i < 3; ++i) p3n2[i] = p3n1[i] = p3n0[i] = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int i = 0; i < 3; ++i) a2n1[i] = make_float2(0.f, 0.f);
-        a4n2_14 = a4n0_14 = 0.f;
+        for (int i = 0; i < 2; ++i) { p2n1[i] = make_float2(0.f, 0.f); s2n1[i] = 0.f; }
+#pragma unroll
+        for (int i = 0; i < 7; ++i) s4n2[i] = s4n0[i] = 0.f;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) s3n2[i] = s3n1[i] = s3n0[i] = 0.f;
     };
     zero_block();
     float* hs = &S.hi[0][0];
     float* ls = &S.lo[0][0];
     // compensated merge of the register block into the shared Kahan pairs (moment order)
     auto merge_block = [&]() {
-        auto merge2 = [&](int base, const float2* v, int npairs) {
+        auto merge = [&](int base, const float2* p, int np, const float* sv, int ns) {
 #pragma unroll
-            for (int i = 0; i < npairs; ++i) {
-                kahan_merge(hs, ls, (base + 2 * i) * kThreads + tid, v[i].x);
-                kahan_merge(hs, ls, (base + 2 * i + 1) * kThreads + tid, v[i].y);
+            for (int i = 0; i < np; ++i) {
+                kahan_merge(hs, ls, (base + 2 * i) * kThreads + tid, p[i].x);
+                kahan_merge(hs, ls, (base + 2 * i + 1) * kThreads + tid, p[i].y);
             }
+#pragma unroll
+            for (int i = 0; i < ns; ++i) kahan_merge(hs, ls, (base + 2 * np + i) * kThreads + tid, sv[i]);
         };
-        merge2(kS4n2, a4n2, 7);
-        kahan_merge(hs, ls, (kS4n2 + 14) * kThreads + tid, a4n2_14);
-        merge2(kS3n2, a3n2, 5);
-        merge2(kS3n1, a3n1, 5);
-        merge2(kS2n1, a2n1, 3);
-        merge2(kS4n0, a4n0, 7);
-        kahan_merge(hs, ls, (kS4n0 + 14) * kThreads + tid, a4n0_14);
-        merge2(kS3n0, a3n0, 5);
+        merge(kS4n2, p4n2, 4, s4n2, 7);
+        merge(kS3n2, p3n2, 3, s3n2, 4);
+        merge(kS3n1, p3n1, 3, s3n1, 4);
+        merge(kS2n1, p2n1, 2, s2n1, 2);
+        merge(kS4n0, p4n0, 4, s4n0, 7);
+        merge(kS3n0, p3n0, 3, s3n0, 4);
         zero_block();
     };
     int blk = 0;   // pairs in the register block (warp-uniform); the block spans tiles
@@ -470,19 +483,20 @@ __global__ void __launch_bounds__(kThreads + 32, 2) build_kernel(BuildArgs a) {
         if (cnt == 0) break;
         const float4* tile = S.tile[slot];
         // exact culling against this warp's sub-brick, compacted in tile order
-        uint16_t* keep = S.keep[warp];
+        float4* keep = S.keep[warp];
         int nkeep = 0;
         for (int base = 0; base < cnt; base += 32) {
             bool near = false;
+            float4 P = make_float4(0.f, 0.f, 0.f, 0.f);
             if (base + lane < cnt) {
-                const float4 P = tile[base + lane];
+                P = tile[base + lane];
                 const float ex = fmaxf(0.f, fmaxf(wlo[0] - P.x, P.x - whi[0]));
                 const float ey = fmaxf(0.f, fmaxf(wlo[1] - P.y, P.y - whi[1]));
                 const float ez = fmaxf(0.f, fmaxf(wlo[2] - P.z, P.z - whi[2]));
                 near = ex * ex + ey * ey + ez * ez <= rc2;
             }
             const unsigned mask = __ballot_sync(0xffffffffu, near);
-            if (near) keep[nkeep + __popc(mask & ((1u << lane) - 1u))] = (uint16_t)(base + lane);
+            if (near) keep[nkeep + __popc(mask & ((1u << lane) - 1u))] = P;
             nkeep += __popc(mask);
         }
         __syncwarp();
@@ -492,55 +506,86 @@ __global__ void __launch_bounds__(kThreads + 32, 2) build_kernel(BuildArgs a) {
             blk += b1 - b0;
 #pragma unroll 4
             for (int l = b0; l < b1; ++l) {
-                const float4 L = tile[keep[l]];
-                const float dx = __fsub_rn(L.x, cx), dy = __fsub_rn(L.y, cy), dz = __fsub_rn(L.z, cz);
+                const float4 L = keep[l];   // (x, y, z, z)
+                // the shell test in rounded single precision, one operation at a time
+                const float2 dxy = sub2(make_float2(L.x, L.y), cxy);
+                const float2 dzz = sub2(make_float2(L.z, L.w), czz);
+                const float dx = dxy.x, dy = dxy.y, dz = dzz.x;
                 const float n2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
                 const bool in = (n2 > rmin2) && (n2 <= rmax2);
                 in_pairs += in ? 1u : 0u;
                 const float r = rsqrtf(n2);
                 const float inv_n = in ? r : 0.f;
-                const float2 xy = mul2(make_float2(dx, dy), make_float2(inv_n, inv_n));
-                const float x = xy.x, y = xy.y, z = dz * inv_n;
-                const float w2 = inv_n * inv_n;
-                const float2 vw2 = make_float2(w2, w2), vn = make_float2(inv_n, inv_n);
-                // degree 2: (xx, yy) (zz, xy) (xz, yz)
-                const float2 m2a = mul2(make_float2(x, y), make_float2(x, y));
-                const float2 m2b = mul2(make_float2(z, x), make_float2(z, y));
-                const float2 m2c = mul2(make_float2(x, y), make_float2(z, z));
-                const float xx = m2a.x, yy = m2a.y, zz = m2b.x, xyv = m2b.y, xz = m2c.x, yz = m2c.y;
-                // degree 3: (xxx, yyy) (zzz, xxy) (xxz, xyy) (yyz, xzz) (yzz, xyz)
-                const float2 m3a = mul2(m2a, make_float2(x, y));
-                const float2 m3b = mul2(make_float2(zz, xx), make_float2(z, y));
-                const float2 m3c = mul2(make_float2(xx, xyv), make_float2(z, y));
-                const float2 m3d = mul2(make_float2(yy, xz), make_float2(z, z));
-                const float2 m3e = mul2(make_float2(yz, xyv), make_float2(z, z));
-                // degree 4: (xxxx, yyyy) (zzzz, xxxy) (xxxz, xyyy) (yyyz, xzzz) (yzzz, xxyy)
-                //           (xxzz, yyzz) (xxyz, xyyz) xyzz
-                const float2 m4a = mul2(m2a, m2a);
-                const float2 m4b = mul2(make_float2(zz, xx), make_float2(zz, xyv));
-                const float2 m4c = mul2(make_float2(xx, yy), make_float2(xz, xyv));
-                const float2 m4d = mul2(make_float2(yy, zz), make_float2(yz, xz));
-                const float2 m4e = mul2(make_float2(zz, xx), make_float2(yz, yy));
-                const float2 m4f = mul2(make_float2(xx, yy), make_float2(zz, zz));
-                const float2 m4g = mul2(make_float2(xx, yy), make_float2(yz, xz));
-                const float m4h = zz * xyv;
-                const float2 m4[7] = {m4a, m4b, m4c, m4d, m4e, m4f, m4g};
-                const float2 m3[5] = {m3a, m3b, m3c, m3d, m3e};
-                const float2 m2[3] = {m2a, m2b, m2c};
-#pragma unroll
-                for (int i = 0; i < 7; ++i) a4n2[i] = fma2(m4[i], vw2, a4n2[i]);
-                a4n2_14 = fmaf(m4h, w2, a4n2_14);
-#pragma unroll
-                for (int i = 0; i < 5; ++i) a3n2[i] = fma2(m3[i], vw2, a3n2[i]);
-#pragma unroll
-                for (int i = 0; i < 5; ++i) a3n1[i] = fma2(m3[i], vn, a3n1[i]);
-#pragma unroll
-                for (int i = 0; i < 3; ++i) a2n1[i] = fma2(m2[i], vn, a2n1[i]);
-#pragma unroll
-                for (int i = 0; i < 7; ++i) a4n0[i] = add2(a4n0[i], m4[i]);
-                a4n0_14 += m4h;
-#pragma unroll
-                for (int i = 0; i < 5; ++i) a3n0[i] = add2(a3n0[i], m3[i]);
+                const float2 rr = make_float2(inv_n, inv_n);
+                // bearing u = (x, y, z) and w = 1/n^2; the x and y halves of the packed pairs are
+                // monomials that differ by exchanging x and y
+                const float2 P1 = mul2(dxy, rr);            // (x, y)
+                const float2 Z1 = mul2(dzz, rr);            // (z, z)
+                const float2 W = mul2(rr, rr);              // (w, w)
+                const float x = P1.x, y = P1.y, z = Z1.x, w = W.x;
+                const float2 P2 = mul2(P1, P1);             // x^2, y^2
+                const float2 PZ = mul2(P1, Z1);             // xz, yz
+                const float2 P3 = mul2(P2, P1);             // x^3, y^3
+                const float2 P2Z = mul2(P2, Z1);            // x^2 z, y^2 z
+                const float2 PZ2 = mul2(PZ, Z1);            // x z^2, y z^2
+                const float z2 = z * z, xy = x * y;
+                const float z3 = z2 * z, x2y = P2.x * y, xy2 = x * P2.y, xyz = xy * z;
+                // degree 3 over n^2 (the degree-4 moments over n^2 are these times one coordinate)
+                const float2 V3 = mul2(P3, W), V2Z = mul2(P2Z, W), VZ2 = mul2(PZ2, W);
+                const float z3w = z3 * w, x2yw = x2y * w, xy2w = xy2 * w, xyzw = xyz * w;
+                // sum u^a / n^2, |a| = 4: x^4 y^4 | x^3z y^3z | x^2z^2 y^2z^2 | xz^3 yz^3 ; z^4 x^3y xy^3 x^2y^2 x^2yz xy^2z xyz^2
+                p4n2[0] = fma2(V3, P1, p4n2[0]);
+                p4n2[1] = fma2(V3, Z1, p4n2[1]);
+                p4n2[2] = fma2(V2Z, Z1, p4n2[2]);
+                p4n2[3] = fma2(VZ2, Z1, p4n2[3]);
+                s4n2[0] = fmaf(z3w, z, s4n2[0]);
+                s4n2[1] = fmaf(V3.x, y, s4n2[1]);
+                s4n2[2] = fmaf(x, V3.y, s4n2[2]);
+                s4n2[3] = fmaf(x2yw, y, s4n2[3]);
+                s4n2[4] = fmaf(x2yw, z, s4n2[4]);
+                s4n2[5] = fmaf(xy2w, z, s4n2[5]);
+                s4n2[6] = fmaf(xyzw, z, s4n2[6]);
+                // sum u^a / n^2, |a| = 3: x^3 y^3 | x^2z y^2z | xz^2 yz^2 ; z^3 x^2y xy^2 xyz
+                p3n2[0] = add2(p3n2[0], V3);
+                p3n2[1] = add2(p3n2[1], V2Z);
+                p3n2[2] = add2(p3n2[2], VZ2);
+                s3n2[0] += z3w;
+                s3n2[1] += x2yw;
+                s3n2[2] += xy2w;
+                s3n2[3] += xyzw;
+                // sum u^a / n, |a| = 3 (same order)
+                p3n1[0] = fma2(P3, rr, p3n1[0]);
+                p3n1[1] = fma2(P2Z, rr, p3n1[1]);
+                p3n1[2] = fma2(PZ2, rr, p3n1[2]);
+                s3n1[0] = fmaf(z3, inv_n, s3n1[0]);
+                s3n1[1] = fmaf(x2y, inv_n, s3n1[1]);
+                s3n1[2] = fmaf(xy2, inv_n, s3n1[2]);
+                s3n1[3] = fmaf(xyz, inv_n, s3n1[3]);
+                // sum u^a / n, |a| = 2: x^2 y^2 | xz yz ; z^2 xy
+                p2n1[0] = fma2(P2, rr, p2n1[0]);
+                p2n1[1] = fma2(PZ, rr, p2n1[1]);
+                s2n1[0] = fmaf(z2, inv_n, s2n1[0]);
+                s2n1[1] = fmaf(xy, inv_n, s2n1[1]);
+                // sum u^a, |a| = 4 (order of the n^2 group)
+                p4n0[0] = fma2(P3, P1, p4n0[0]);
+                p4n0[1] = fma2(P3, Z1, p4n0[1]);
+                p4n0[2] = fma2(P2Z, Z1, p4n0[2]);
+                p4n0[3] = fma2(PZ2, Z1, p4n0[3]);
+                s4n0[0] = fmaf(z3, z, s4n0[0]);
+                s4n0[1] = fmaf(P3.x, y, s4n0[1]);
+                s4n0[2] = fmaf(x, P3.y, s4n0[2]);
+                s4n0[3] = fmaf(x2y, y, s4n0[3]);
+                s4n0[4] = fmaf(x2y, z, s4n0[4]);
+                s4n0[5] = fmaf(xy2, z, s4n0[5]);
+                s4n0[6] = fmaf(xyz, z, s4n0[6]);
+                // sum u^a, |a| = 3
+                p3n0[0] = add2(p3n0[0], P3);
+                p3n0[1] = add2(p3n0[1], P2Z);
+                p3n0[2] = add2(p3n0[2], PZ2);
+                s3n0[0] += z3;
+                s3n0[1] += x2y;
+                s3n0[2] += xy2;
+                s3n0[3] += xyz;
             }
             b0 = b1;
             if (blk == kBlock) {
@@ -649,7 +694,9 @@ int launch_build(const BuildArgs& a, cudaStream_t stream) {
     const int smem = (int)sizeof(BuildSmem);
     if (cudaFuncSetAttribute(build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return FIF_ECUDA;
-    const int64_t bricks = (int64_t)((a.nx + kBX - 1) / kBX) * ((a.ny + kBY - 1) / kBY) * ((a.nz + kBZ - 1) / kBZ);
+    const int bz0 = a.k_begin / kBZ, bz1 = (a.k_end + kBZ - 1) / kBZ;
+    const int64_t bricks = (int64_t)((a.nx + kBX - 1) / kBX) * ((a.ny + kBY - 1) / kBY) * (bz1 - bz0);
+    if (bricks <= 0) return FIF_OK;
     if (bricks > (int64_t)INT32_MAX) return FIF_ERANGE;
     build_kernel<<<(unsigned)bricks, kThreads + 32, smem, stream>>>(a);
     return cudaPeekAtLastError() == cudaSuccess ? FIF_OK : FIF_ECUDA;

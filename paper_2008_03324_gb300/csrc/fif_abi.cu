@@ -215,21 +215,49 @@ size_t fif_build_workspace_bytes(const fif_field* field, int64_t n) {
 }
 
 static int32_t build_impl(fif_field* field, const float* d_landmarks, int64_t n, void* d_ws, size_t ws_bytes,
-                          int accumulate, fif_stream_t stream);
+                          int accumulate, int k_begin, int k_end, fif_stream_t stream);
 
 int32_t fif_build(fif_field* field, const float* d_landmarks, int64_t n, void* d_ws, size_t ws_bytes,
                   fif_stream_t stream) {
-    return build_impl(field, d_landmarks, n, d_ws, ws_bytes, 0, stream);
+    if (!field) return FIF_EINVAL;
+    return build_impl(field, d_landmarks, n, d_ws, ws_bytes, 0, 0, field->grid.nz, stream);
 }
 
 int32_t fif_build_update(fif_field* field, const float* d_landmarks, int64_t n, int32_t sign, void* d_ws,
                          size_t ws_bytes, fif_stream_t stream) {
     if (sign != 1 && sign != -1) return FIF_EINVAL;
-    return build_impl(field, d_landmarks, n, d_ws, ws_bytes, sign, stream);
+    if (!field) return FIF_EINVAL;
+    return build_impl(field, d_landmarks, n, d_ws, ws_bytes, sign, 0, field->grid.nz, stream);
+}
+
+int32_t fif_build_slab(fif_field* field, int32_t k_begin, int32_t k_end, const float* d_landmarks, int64_t n,
+                       void* d_ws, size_t ws_bytes, fif_stream_t stream) {
+    if (!field) return FIF_EINVAL;
+    if (k_begin < 0 || k_end <= k_begin || k_end > field->grid.nz) return FIF_EINVAL;
+    return build_impl(field, d_landmarks, n, d_ws, ws_bytes, 0, k_begin, k_end, stream);
+}
+
+int32_t fif_slab_landmark_band(const fif_field* field, int32_t k_begin, int32_t k_end, float* z_lo, float* z_hi) {
+    int rc = check_field(field);
+    if (rc) return rc;
+    if (!z_lo || !z_hi || k_begin < 0 || k_end <= k_begin || k_end > field->grid.nz) return FIF_EINVAL;
+    // the node layers of the bricks that hold the slab's nodes (a warp's culling box may span layers
+    // just outside the slab), widened by the build's cull radius (a landmark farther than that from
+    // every node of a box never enters the sums), plus 1e-3 relative and 1 mm for the
+    // single-precision rounding of positions and of the culling test
+    const int bz = field->storage == FIF_STORAGE_GP ? fif::kGpBuildBrickZ : fif::kBuildBrickZ;
+    const int kb0 = k_begin / bz * bz, kb1 = std::min((k_end + bz - 1) / bz * bz, (int)field->grid.nz);
+    const double z0 = (double)field->grid.origin[2] + (double)field->grid.res * kb0;
+    const double z1 = (double)field->grid.origin[2] + (double)field->grid.res * (kb1 - 1);
+    const double r_cull = field->params.r_max + 0.01 + 1e-4 * field->params.r_max;
+    const double m = r_cull * 1.001 + 1e-3 + 1e-6 * std::max(std::fabs(z0), std::fabs(z1));
+    *z_lo = (float)(z0 - m);
+    *z_hi = (float)(z1 + m);
+    return FIF_OK;
 }
 
 static int32_t build_impl(fif_field* field, const float* d_landmarks, int64_t n, void* d_ws, size_t ws_bytes,
-                          int accumulate, fif_stream_t stream) {
+                          int accumulate, int k_begin, int k_end, fif_stream_t stream) {
     int rc = check_field(field);
     if (rc) return rc;
     if (n < 0 || (n > 0 && !d_landmarks) || !d_ws) return FIF_EINVAL;
@@ -256,6 +284,8 @@ static int32_t build_impl(fif_field* field, const float* d_landmarks, int64_t n,
     a.err = device_error_ptr();
     a.accumulate = accumulate;
     a.wait_ns = g_wait_ns.load(std::memory_order_relaxed);
+    a.k_begin = k_begin;
+    a.k_end = k_end;
     if (field->storage == FIF_STORAGE_GP) {
         const fif_gp& gp = field->gp;
         const fif::GpAuxLayout L = fif::gp_aux_layout(gp.n_samples, fif_gp_row_stride(gp.n_samples));
@@ -274,7 +304,8 @@ int32_t fif_query(const fif_field* field, const float* d_poses, int64_t m, int32
     int rc = check_field(field);
     if (rc) return rc;
     if (m < 0 || (m > 0 && !d_poses)) return FIF_EINVAL;
-    if (flags & ~(FIF_Q_NEAREST | FIF_Q_WORLD | FIF_Q_METRICS)) return FIF_EINVAL;
+    if (flags & ~(FIF_Q_NEAREST | FIF_Q_WORLD | FIF_Q_METRICS | FIF_Q_GP_COMPENSATED)) return FIF_EINVAL;
+    if ((flags & FIF_Q_GP_COMPENSATED) && field->storage != FIF_STORAGE_GP) return FIF_EINVAL;
     if (m == 0) return FIF_OK;   // nothing to write (empty buffers may be NULL)
     if ((flags & FIF_Q_METRICS) && !d_metrics && !d_sign && !d_status) return FIF_EINVAL;
     if (reinterpret_cast<uintptr_t>(d_poses) & 3u) return FIF_EALIGN;

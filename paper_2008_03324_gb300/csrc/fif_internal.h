@@ -64,13 +64,17 @@ struct BinGrid {
 };
 
 struct BuildLayout {
-    size_t sorted;   // float4[n]  (x, y, z, index bits)
+    size_t sorted;   // float4[n]  (x, y, z, input index bits) while sorting, then (x, y, z, z)
     size_t binof;    // int32[n]
     size_t count;    // int32[nbins]  (count, then cursor)
     size_t start;    // int32[nbins + 1]
     size_t stats;    // uint64[4]  (in-shell pairs, candidate pairs, dropped landmarks, -)
     size_t total;
 };
+
+// z-depth (node layers) of the bricks a CTA of the quadratic / trace build and of the GP build owns
+constexpr int kBuildBrickZ = 4;
+constexpr int kGpBuildBrickZ = 2;
 
 BinGrid make_bin_grid(const fif_field* f);
 BuildLayout build_layout(const BinGrid& bg, int64_t n);
@@ -91,6 +95,7 @@ struct BuildArgs {
     int* err;
     int accumulate;   // 0: overwrite the field; +1 / -1: add / subtract these landmarks' share
     uint64_t wait_ns; // limit of each bounded device wait (fif_set_wait_limit)
+    int k_begin, k_end;   // only nodes with k_begin <= k < k_end are built (a z-slab; 0, nz: all)
     // GP visibility field (storage FIF_STORAGE_GP): v^s_g = 1 / (1 + 2^(gp_shift - gp_scale z_g.u))
     const float4* gp_axes;    // [ns] (x, y, z, 0)
     int gp_ns, gp_rs;

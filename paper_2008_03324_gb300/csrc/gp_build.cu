@@ -82,12 +82,13 @@ __global__ void __launch_bounds__(kGbThreads + 32, 1) gp_build_kernel(BuildArgs 
     GpBuildSmem<G>& S = *reinterpret_cast<GpBuildSmem<G>*>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
+    static_assert(kGpBuildBrickZ == 2, "a GP brick is 4 x 2 x 2 nodes");
     const int nbx = (a.nx + 3) / 4, nby = (a.ny + 1) / 2;
-    const int brick = blockIdx.x;
+    const int brick = blockIdx.x + (a.k_begin / 2) * nbx * nby;   // z-bricks meeting the slab
     const int i0 = 4 * (brick % nbx), j0 = 2 * ((brick / nbx) % nby), k0 = 2 * (brick / (nbx * nby));
     const int ni = i0 + (warp & 3), nj = j0 + ((warp >> 2) & 1), nk = k0 + (warp >> 3);
     const bool producer = warp == kGbWarps;   // the 17th warp streams the landmark tiles
-    const bool valid = !producer && ni < a.nx && nj < a.ny && nk < a.nz;
+    const bool valid = !producer && ni < a.nx && nj < a.ny && nk < a.nz && nk >= a.k_begin && nk < a.k_end;
     const float cx = __fadd_rn(a.ox, __fmul_rn(a.res, (float)ni));
     const float cy = __fadd_rn(a.oy, __fmul_rn(a.res, (float)nj));
     const float cz = __fadd_rn(a.oz, __fmul_rn(a.res, (float)nk));
@@ -351,7 +352,8 @@ static int launch_gp_build_g(const BuildArgs& a, cudaStream_t stream) {
     const int smem = (int)sizeof(GpBuildSmem<G>);
     if (cudaFuncSetAttribute(gp_build_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return FIF_ECUDA;
-    const int64_t bricks = (int64_t)((a.nx + 3) / 4) * ((a.ny + 1) / 2) * ((a.nz + 1) / 2);
+    const int64_t bricks = (int64_t)((a.nx + 3) / 4) * ((a.ny + 1) / 2) * ((a.k_end + 1) / 2 - a.k_begin / 2);
+    if (bricks <= 0) return FIF_OK;
     if (bricks > (int64_t)INT32_MAX) return FIF_ERANGE;
     gp_build_kernel<G><<<(unsigned)bricks, kGbThreads + 32, smem, stream>>>(a);
     return cudaPeekAtLastError() == cudaSuccess ? FIF_OK : FIF_ECUDA;

@@ -19,7 +19,8 @@
 // Query (gp_query_kernel): a persistent CTA walks groups of 32 poses with three warp roles:
 //  contract (4 warps)  warp p streams the x-adjacent corner pair p of each pose (one bulk copy
 //                      of both node records into its own ring), lane e < 21 forms
-//                      w_j sum_g a_g D_g[e] for both corners;
+//                      w_j sum_g a_g D_g[e] for both corners (in single precision, or as a
+//                      compensated dot product with FIF_Q_GP_COMPENSATED);
 //  weights  (8 warps)  K_z in double-float arithmetic, a(z) = W K_z as compensated
 //                      single-precision sums with W split into high and low parts
 //                      (two-product / two-sum);
@@ -229,8 +230,33 @@ FIF_DEV void df_fma2(float2 Wh, float2 Whn, float2 Wl, float2 Kh, float2 Kl, flo
     lo = add2(lo, add2(err, e));
 }
 
-// NB table buffers and as many metric warps: group k uses buffer k mod NB
-template <int G, int NB>
+// One step of the compensated dot product on packed pairs: (s, e) += a v, where an = -a.
+// fl(a v) is formed negated (exact), its rounding error a v - fl(a v) exactly by an fma, the sum
+// s + fl(a v) by Knuth's two-sum; both errors go to e.
+FIF_DEV void dot2_step(float2 a, float2 an, float2 v, float2& s, float2& e) {
+    const float2 pn = mul2(an, v);                      // -fl(a v)
+    const float2 pe = fma2(a, v, pn);                   // a v - fl(a v)
+    const float2 sn = sub2(s, pn);                      // fl(s + fl(a v))
+    const float2 bb = sub2(sn, s);
+    const float2 err = sub2(sub2(s, sub2(sn, bb)), add2(pn, bb));   // (s - (sn - bb)) + (p - bb)
+    s = sn;
+    e = add2(e, add2(err, pe));
+}
+
+// two compensated packed sums (s, e) and (t, f) combined into one float: the four partial sums
+// by two-sums, then all rounding errors added
+FIF_DEV float dot2_finish(float2 s, float2 e, float2 t, float2 f) {
+    float h0, l0, h1, l1, h, l;
+    two_sum(s.x, s.y, h0, l0);
+    two_sum(t.x, t.y, h1, l1);
+    two_sum(h0, h1, h, l);
+    const float err = __fadd_rn(__fadd_rn(__fadd_rn(l0, l1), l), __fadd_rn(__fadd_rn(e.x, e.y), __fadd_rn(f.x, f.y)));
+    return __fadd_rn(h, err);
+}
+
+// group k uses table buffer k mod NB
+// NB table buffers and as many metric warps; kComp: compensated contraction (FIF_Q_GP_COMPENSATED)
+template <int G, int NB, bool kComp>
 __global__ void __launch_bounds__((kGqContract + kGqWeights + NB) * 32, 1) gp_query_kernel(QueryArgs a, GqLayout L) {
     constexpr int kThreads = (kGqContract + kGqWeights + NB) * 32;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -326,30 +352,64 @@ __global__ void __launch_bounds__((kGqContract + kGqWeights + NB) * 32, 1) gp_qu
             if (!gq_wait(&B.full[jp][it % NS], (uint32_t)((it / NS) & 1), flag, a.err)) break;
             const int4 te = mytab[b * 32 + i];
             if (lane < 21) {
-                // both corners of the pair at once: each weight pair is loaded once, four
-                // independent accumulators keep several shared-memory loads in flight
                 const float2* av = reinterpret_cast<const float2*>(atab + (b * 32 + i) * rs);
                 const float2* r0 = reinterpret_cast<const float2*>(myring + (it % NS) * S2 + lane * rs);
                 const float2* r1 = reinterpret_cast<const float2*>(myring + (it % NS) * S2 + S + lane * rs);
-                float2 a0 = make_float2(0.f, 0.f), a1 = a0, c0 = a0, c1 = a0;
+                const float2 zero = make_float2(0.f, 0.f);
                 const int n2 = rs >> 1;
-                int g2 = 0;
+                float v0, v1;
+                if constexpr (kComp) {
+                    // entry e = lane of sum_g a_g D_g for both corners of the pair as a compensated
+                    // dot product (Ogita, Rump and Oishi, "Accurate sum and dot product", SIAM J.
+                    // Sci. Comput. 26(6), 2005, Algorithm Dot2): each product split exactly with an
+                    // fma, each addition with Knuth's two-sum, the rounding errors summed apart, so
+                    // the result is as accurate as if carried in twice the precision although the
+                    // weights a_g change sign and cancel.  Packed pairs run over (g, g + 1); two
+                    // independent chains per corner (even and odd pairs of g).
+                    const float2 neg1 = make_float2(-1.f, -1.f);
+                    float2 s0 = zero, e0 = zero, s1 = zero, e1 = zero, t0 = zero, f0 = zero, t1 = zero, f1 = zero;
+                    int g2 = 0;
+                    for (; g2 + 1 < n2; g2 += 2) {
+                        const float2 ag = av[g2], ah = av[g2 + 1];
+                        const float2 an = mul2(ag, neg1), hn = mul2(ah, neg1);
+                        dot2_step(ag, an, r0[g2], s0, e0);
+                        dot2_step(ag, an, r1[g2], s1, e1);
+                        dot2_step(ah, hn, r0[g2 + 1], t0, f0);
+                        dot2_step(ah, hn, r1[g2 + 1], t1, f1);
+                    }
+                    if (g2 < n2) {
+                        const float2 ag = av[g2];
+                        const float2 an = mul2(ag, neg1);
+                        dot2_step(ag, an, r0[g2], s0, e0);
+                        dot2_step(ag, an, r1[g2], s1, e1);
+                    }
+                    v0 = dot2_finish(s0, e0, t0, f0);
+                    v1 = dot2_finish(s1, e1, t1, f1);
+                } else {
+                    // both corners of the pair at once in single precision: each weight pair is
+                    // loaded once, four independent accumulators keep several shared-memory loads
+                    // in flight
+                    float2 a0 = zero, a1 = zero, c0 = zero, c1 = zero;
+                    int g2 = 0;
 #pragma unroll 4
-                for (; g2 + 1 < n2; g2 += 2) {
-                    const float2 v0 = av[g2], v1 = av[g2 + 1];
-                    a0 = fma2(r0[g2], v0, a0);
-                    a1 = fma2(r0[g2 + 1], v1, a1);
-                    c0 = fma2(r1[g2], v0, c0);
-                    c1 = fma2(r1[g2 + 1], v1, c1);
-                }
-                if (g2 < n2) {
-                    const float2 v0 = av[g2];
-                    a0 = fma2(r0[g2], v0, a0);
-                    c0 = fma2(r1[g2], v0, c0);
+                    for (; g2 + 1 < n2; g2 += 2) {
+                        const float2 w0 = av[g2], w1 = av[g2 + 1];
+                        a0 = fma2(r0[g2], w0, a0);
+                        a1 = fma2(r0[g2 + 1], w1, a1);
+                        c0 = fma2(r1[g2], w0, c0);
+                        c1 = fma2(r1[g2 + 1], w1, c1);
+                    }
+                    if (g2 < n2) {
+                        const float2 w0 = av[g2];
+                        a0 = fma2(r0[g2], w0, a0);
+                        c0 = fma2(r1[g2], w0, c0);
+                    }
+                    v0 = (a0.x + a0.y) + (a1.x + a1.y);
+                    v1 = (c0.x + c0.y) + (c1.x + c1.y);
                 }
                 float* er = eb + (b * 32 + i) * kEbRow + 2 * jp * 21 + lane;
-                er[0] = __int_as_float(te.z) * ((a0.x + a0.y) + (a1.x + a1.y));
-                er[21] = __int_as_float(te.w) * ((c0.x + c0.y) + (c1.x + c1.y));
+                er[0] = __int_as_float(te.z) * v0;
+                er[21] = __int_as_float(te.w) * v1;
             }
             __syncwarp();
             if (i == 31 || gq_stream(it + 1, m) < 0) {
@@ -564,16 +624,22 @@ __global__ void __launch_bounds__((kGqContract + kGqWeights + NB) * 32, 1) gp_qu
 
 }  // namespace
 
-template <int G, int NB>
-static int launch_gp_query_nb(const QueryArgs& a, const GqLayout& L, int sms, cudaStream_t stream) {
-    if (cudaFuncSetAttribute(gp_query_kernel<G, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total) !=
-        cudaSuccess)
+template <int G, int NB, bool kComp>
+static int launch_gp_query_kc(const QueryArgs& a, const GqLayout& L, int sms, cudaStream_t stream) {
+    auto kern = gp_query_kernel<G, NB, kComp>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total) != cudaSuccess)
         return FIF_ECUDA;
     const int64_t groups = (a.m + 31) / 32;
     const int64_t grid = std::min<int64_t>(groups, (int64_t)sms);
     if (grid <= 0) return FIF_OK;
-    gp_query_kernel<G, NB><<<(unsigned)grid, (kGqContract + kGqWeights + NB) * 32, L.total, stream>>>(a, L);
+    kern<<<(unsigned)grid, (kGqContract + kGqWeights + NB) * 32, L.total, stream>>>(a, L);
     return cudaPeekAtLastError() == cudaSuccess ? FIF_OK : FIF_ECUDA;
+}
+
+template <int G, int NB>
+static int launch_gp_query_nb(const QueryArgs& a, const GqLayout& L, int sms, cudaStream_t stream) {
+    return (a.flags & FIF_Q_GP_COMPENSATED) ? launch_gp_query_kc<G, NB, true>(a, L, sms, stream)
+                                            : launch_gp_query_kc<G, NB, false>(a, L, sms, stream);
 }
 
 template <int G>

@@ -1,8 +1,11 @@
 """Multi-process helpers (one process per GPU, launched by torchrun).
 
 The query path shards with no data-path exchange: every rank holds a replica of the field
-and answers its own slice of the poses (weak scaling).  The only collectives are the
-timing barrier and the max-over-ranks of the measured time."""
+and answers its own slice of the poses (weak scaling).  The build shards by z-slabs of the
+lattice (Sec. VI-A-1: every node is independent): each rank builds its slab from the landmarks
+in the slab's band (fif_slab_landmark_band), and one broadcast per rank of its slab, the only
+data exchange, completes every replica.  The other collectives are the timing barrier and the
+max-over-ranks of the measured time."""
 from __future__ import annotations
 
 import os
@@ -54,3 +57,31 @@ def sum_over_ranks(x: float, device=None) -> float:
     t = torch.tensor([float(x)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def slab_ranges(nz: int, world_size: int, align: int = 4) -> list[tuple[int, int]]:
+    """Contiguous z-slabs [k_begin, k_end) of an nz-layer lattice, one per rank, cut at multiples
+    of `align` (the build's brick depth, so no brick is shared) while there are enough layers; a
+    rank may get an empty slab (k_begin == k_end) when there are more ranks than bricks."""
+    bricks = -(-nz // align)
+    out = []
+    for r in range(world_size):
+        b0, b1 = shard(bricks, r, world_size)
+        out.append((min(nz, b0 * align), min(nz, b1 * align)))
+    return out
+
+
+def slab_landmarks(landmarks, band):
+    """The landmarks whose z lies in band = (z_lo, z_hi), in their input order (numpy [n, 3])."""
+    z = landmarks[:, 2]
+    return landmarks[(z >= band[0]) & (z <= band[1])]
+
+
+def gather_slabs(coeffs: torch.Tensor, ranges, nodes_per_layer: int):
+    """Complete every rank's copy of the node-major storage coeffs [n_nodes, stride]: rank r
+    broadcasts its rows [k_begin * nx ny, k_end * nx ny)."""
+    if not (dist.is_available() and dist.is_initialized()):
+        return
+    for r, (k0, k1) in enumerate(ranges):
+        if k1 > k0:
+            dist.broadcast(coeffs[k0 * nodes_per_layer:k1 * nodes_per_layer], src=r)

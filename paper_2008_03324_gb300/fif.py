@@ -31,7 +31,7 @@ POSE_OUTSIDE, POSE_QUAT, POSE_NOT_PD, POSE_NAN = 1, 2, 4, 8
 STORAGE_F32, STORAGE_BF16, STORAGE_TRACE, STORAGE_GP = 0, 1, 2, 3
 MODEL_POINTCLOUD, MODEL_QUAD, MODEL_GP = 0, 1, 2
 GP_MAX_SAMPLES = 96
-Q_TRILINEAR, Q_NEAREST, Q_CAMERA, Q_WORLD = 0x0, 0x1, 0x0, 0x2
+Q_TRILINEAR, Q_NEAREST, Q_CAMERA, Q_WORLD, Q_GP_COMPENSATED = 0x0, 0x1, 0x0, 0x2, 0x4
 Q_TRACE, Q_LOGDET, Q_LMIN, Q_METRICS = 0x10, 0x20, 0x40, 0x70
 STRIDE = {STORAGE_F32: 216, STORAGE_BF16: 224, STORAGE_TRACE: 12}
 
@@ -85,6 +85,9 @@ _SIGS = {
     "fif_build_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(FieldC), _I64]),
     "fif_build": (_I32, [ctypes.POINTER(FieldC), _VP, _I64, _VP, ctypes.c_size_t, _VP]),
     "fif_build_static": (_I32, [ctypes.POINTER(FieldC), _VP, _I64, _VP]),
+    "fif_build_slab": (_I32, [ctypes.POINTER(FieldC), _I32, _I32, _VP, _I64, _VP, ctypes.c_size_t, _VP]),
+    "fif_slab_landmark_band": (_I32, [ctypes.POINTER(FieldC), _I32, _I32, ctypes.POINTER(ctypes.c_float),
+                                      ctypes.POINTER(ctypes.c_float)]),
     "fif_build_update": (_I32, [ctypes.POINTER(FieldC), _VP, _I64, _I32, _VP, ctypes.c_size_t, _VP]),
     "fif_query": (_I32, [ctypes.POINTER(FieldC), _VP, _I64, _I32, _VP, _VP, _VP, _VP, _VP]),
     "fif_query_host_staging_bytes": (ctypes.c_size_t, [_I64]),
@@ -338,6 +341,23 @@ def build_update(field: FieldC, landmarks: torch.Tensor, sign: int, workspace: t
     _check(lib().fif_build_update(ctypes.byref(field), _ptr(landmarks), landmarks.shape[0], int(sign),
                                   _ptr(workspace), workspace.numel() * workspace.element_size(), _stream(stream)),
            "fif_build_update")
+
+
+def build_slab(field: FieldC, k_begin: int, k_end: int, landmarks: torch.Tensor, workspace: torch.Tensor,
+               stream=None):
+    """fif_build_slab: build only the nodes with k_begin <= k < k_end."""
+    assert landmarks.is_cuda and landmarks.dtype == torch.float32 and landmarks.is_contiguous()
+    _check(lib().fif_build_slab(ctypes.byref(field), int(k_begin), int(k_end), _ptr(landmarks), landmarks.shape[0],
+                                _ptr(workspace), workspace.numel() * workspace.element_size(), _stream(stream)),
+           "fif_build_slab")
+
+
+def slab_landmark_band(field: FieldC, k_begin: int, k_end: int):
+    """fif_slab_landmark_band: (z_lo, z_hi) of the landmarks the slab's build can use (host only)."""
+    lo, hi = ctypes.c_float(0.0), ctypes.c_float(0.0)
+    _check(lib().fif_slab_landmark_band(ctypes.byref(field), int(k_begin), int(k_end), ctypes.byref(lo),
+                                        ctypes.byref(hi)), "fif_slab_landmark_band")
+    return float(lo.value), float(hi.value)
 
 
 BUILD_STATIC_SCRATCH_BYTES = 16 << 20

@@ -94,6 +94,9 @@ def test_calls_reject_bad_arguments_before_any_launch(F):
     assert lib.fif_query(ctypes.byref(f), None, -1, F.Q_METRICS, None, None, None, None, None) == F.EINVAL
     assert lib.fif_query(ctypes.byref(f), None, 5, F.Q_METRICS, None, None, None, None, None) == F.EINVAL
     assert lib.fif_query(ctypes.byref(f), fake, 5, 0x1000, None, None, None, None, None) == F.EINVAL
+    # the compensated contraction is a GP-field option only
+    assert lib.fif_query(ctypes.byref(f), fake, 5, F.Q_METRICS | F.Q_GP_COMPENSATED, None, fake, None, None,
+                         None) == F.EINVAL
     assert lib.fif_query(ctypes.byref(f), fake, 0, F.Q_METRICS, None, fake, None, None, None) == F.OK
     assert lib.fif_query_backward(ctypes.byref(f), fake, 5, F.Q_NEAREST, fake, fake, fake, None) == F.EINVAL
     assert lib.fif_build(ctypes.byref(f), None, 5, fake, 1 << 20, None) == F.EINVAL

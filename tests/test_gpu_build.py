@@ -194,3 +194,41 @@ def test_trace_factor_field(F):
     _, met_full, _, _ = full.query(torch.from_numpy(poses).cuda(), F.Q_TRACE | F.Q_WORLD)
     torch.cuda.synchronize()
     assert np.all(np.abs(met[:, 0].cpu().numpy() - met_full[:, 0].cpu().numpy()) <= t_tr)
+
+
+@pytest.mark.parametrize("case", ["tall_room", "warehouse"])
+def test_slab_builds_reproduce_the_whole_field_bitwise(F, case):
+    """fif_build_slab (Sec. VI-A-1, nodes independent): z-slabs built apart, each from only the
+    landmarks in its band, reproduce the whole-lattice build bitwise; nodes outside a slab keep
+    their contents.  The bands cut the maps (range shells of 2.5 m and 3 m)."""
+    from paper_2008_03324_gb300 import dist
+    if case == "tall_room":
+        spec = synth.GridSpec((0.0, 0.0, 0.0), 0.5, (9, 9, 25))
+        lm_np = synth.room_landmarks(seed=4, n=4000, size=(4.0, 4.0, 12.0)).landmarks
+        r_max, cuts = 2.5, [(0, 8), (8, 13), (13, 25)]
+    else:
+        spec = X.WAREHOUSE["grid"]
+        lm_np = X.warehouse_scene().landmarks
+        r_max, cuts = 3.0, dist.slab_ranges(spec.dims[2], 2)
+    lm = torch.from_numpy(lm_np).cuda()
+    whole, _ = gpu_build(F, lm_np, spec, r_max)
+    slabbed = F.Field(spec.origin, spec.res, spec.dims, F.make_params(r_max=r_max))
+    slabbed.coeffs.fill_(float("nan"))
+    nxy = spec.dims[0] * spec.dims[1]
+    for k0, k1 in cuts:
+        band = F.slab_landmark_band(slabbed.c, k0, k1)
+        sub = torch.from_numpy(np.ascontiguousarray(dist.slab_landmarks(lm_np, band))).cuda()
+        assert sub.shape[0] < lm.shape[0]
+        ws = torch.empty(F.build_workspace_bytes(slabbed.c, sub.shape[0]), dtype=torch.uint8, device="cuda")
+        before = slabbed.coeffs.clone()
+        F.build_slab(slabbed.c, k0, k1, sub, ws)
+        torch.cuda.synchronize()
+        assert F.device_error() == 0
+        rows = slice(k0 * nxy, k1 * nxy)
+        assert torch.equal(slabbed.coeffs[rows], whole.coeffs[rows])
+        outside = torch.ones(spec.n_nodes, dtype=torch.bool, device="cuda")
+        outside[rows] = False
+        assert torch.equal(slabbed.coeffs[outside].isnan(), before[outside].isnan())
+    assert torch.equal(slabbed.coeffs, whole.coeffs)
+    with pytest.raises(F.FifError):
+        F.build_slab(slabbed.c, 3, 3, lm, ws)

@@ -71,7 +71,10 @@ def test_warehouse_gp_query_2m22_sampled(F, setup):
     """GP field (N_s = 70, length scale fitted as the bench does), 2^22 poses, 48 sampled poses
     against the oracle: corner coefficients from the oracle's sigmoid basis D (node frame), moved
     to the world frame and to the paper's basis C = W D (both exact, pinned on the CPU), then
-    the oracle's GP query.  Tolerance as in tests/test_gpu_gp.py end to end: max(1e-5, 2e-5 kappa)."""
+    the oracle's GP query.  Tolerance as in tests/test_gpu_gp.py end to end: max(1e-5, 2e-5 kappa);
+    then the oracle's D written into the field at those poses' corner nodes and the same launch
+    again, within the query's own bounds: max(1e-5, 16 u kappa) with the single-precision
+    contraction, max(1e-5, 2 u kappa) with the compensated one."""
     sc, spec, poses, sample = setup
     axes = synth.fibonacci_sphere(70)
     l = F.gp_fit_length_scale(axes, synth.sphere_points(7, 2000))
@@ -82,8 +85,7 @@ def test_warehouse_gp_query_2m22_sampled(F, setup):
     fim, met, st = run_query(F, field, poses, F.Q_METRICS)
     sub = sample[np.linspace(0, len(sample) - 1, 48).astype(int)]
     got = X.unpack21(fim[torch.from_numpy(sub).cuda()].cpu().numpy())
-    del field
-    torch.cuda.empty_cache()
+    del fim, met, st
     ogp = O.GP(axes, l)
     grid = X.oracle_grid(spec)
     nodes, w, _, _ = O.query_cells(grid, poses[sub])
@@ -114,5 +116,27 @@ def test_warehouse_gp_query_2m22_sampled(F, setup):
         kap[i] = s / max(X.fro(I_ref[i]), 1e-300)
     tau = np.maximum(X.TAU_F32, 2 * X.TAU_F32 * kap)
     err = X.rel_fro(got, I_ref)
+    # the query's own arithmetic in the same 2^22-pose launch: the oracle's D written into the
+    # field at every node these poses touch, bound max(1e-5, 2 u kappa) as in tests/test_gpu_gp.py
+    from tests.test_gpu_gp import pack_gp
+    field.coeffs[torch.from_numpy(uniq).cuda()] = torch.from_numpy(
+        pack_gp(D, F.gp_row_stride(70), F.gp_stride(70))).cuda()
+    u = 2.0 ** -24
+    errs = {}
+    for comp in (False, True):
+        fim, _, _ = run_query(F, field, poses, F.Q_METRICS | (F.Q_GP_COMPENSATED if comp else 0))
+        errs[comp] = X.rel_fro(X.unpack21(fim[torch.from_numpy(sub).cuda()].cpu().numpy()), I_ref)
+        del fim
+    del field
+    torch.cuda.empty_cache()
+    msg = (f"GP query N_s = 70, 2^22 poses, {len(sub)} sampled poses; kappa median {np.median(kap):.1f} p99 "
+           f"{np.percentile(kap, 99):.1f} max {kap.max():.1f}; GPU build + query: error max {err.max():.2e} p99 "
+           f"{np.percentile(err, 99):.2e} median {np.median(err):.2e}")
+    for comp, e in errs.items():
+        msg += (f"; oracle D + GPU query, {'compensated' if comp else 'single-precision'}: error max {e.max():.2e} "
+                f"p99 {np.percentile(e, 99):.2e}, max error / (u kappa) {(e / (u * kap)).max():.2f}")
+    print(msg)
     assert np.all(err <= tau), (err.max(), (err / tau).max())
     assert np.median(err) <= X.TAU_F32
+    assert np.all(errs[False] <= np.maximum(X.TAU_F32, 16 * u * kap)), msg
+    assert np.all(errs[True] <= np.maximum(X.TAU_F32, 2 * u * kap)), msg

@@ -8,10 +8,14 @@ Frobenius error <= 1e-5 per node, as for the quadratic field.  The query forms
 I = sum_j w_j sum_g a_g(z) D_g(c_j) moved to the camera; storage rounding of D (unit roundoff
 u = 2^-24) reaches I amplified by the contraction's condition number
     kappa = sum_j w_j (1 + |c_j - t|)^2 sum_g |a_g| ||D_g(c_j)||_F / ||I||_F
-(the weights a_g change sign; (1 + |d|)^2 bounds the norm of the move by d), so a pose passes
-when its error is within max(1e-5, 16 u kappa): storage, the rounding of a and the
-single-precision contraction each contribute a few u kappa.  End to end the per-node build error
-(<= 1e-5) is amplified the same way: max(1e-5, 2e-5 kappa)."""
+(the weights a_g change sign; (1 + |d|)^2 bounds the norm of the move by d).  Storage rounds
+every entry of D by at most u/2 (u kappa / 2), the single-precision a_g by at most u/2 (another
+u kappa / 2); the moves and the rotation that follow act on the contracted, already cancelled
+matrices (errors of order u ||I||, inside the 1e-5 floor).  The default single-precision
+contraction adds a summation error of a few u kappa: a pose passes within max(1e-5, 16 u kappa).
+With FIF_Q_GP_COMPENSATED the contraction is a compensated dot product whose own error is of
+order u ||I||: within max(1e-5, 2 u kappa).  End to end the per-node build error (<= 1e-5) is
+amplified the same way: max(1e-5, 2e-5 kappa)."""
 import functools
 import math
 
@@ -261,16 +265,25 @@ def oracle_gp_query(ns, poses, frame=O.FRAME_CAMERA, interp=O.INTERP_TRILINEAR):
     return I
 
 
+@pytest.mark.parametrize("comp", [False, True])
 @pytest.mark.parametrize("ns", [30, 70])
-def test_gp_query_uploaded_room(F, ns):
+def test_gp_query_uploaded_room(F, ns, comp):
     """1000 random room poses (31 full groups of 32 and a ragged tail of 8) on the oracle's own
-    D, camera frame: the query's arithmetic alone against the oracle's paper-basis query."""
+    D, camera frame: the query's arithmetic alone against the oracle's paper-basis query, with
+    the single-precision and the compensated contraction."""
     field = uploaded(F, ns)
     poses = X.room_poses(1000)
-    fim, met, sg, st = run(F, field, poses)
+    fim, met, sg, st = run(F, field, poses, F.Q_METRICS | (F.Q_GP_COMPENSATED if comp else 0))
     I_ref = oracle_gp_query(ns, poses)
-    tau = np.maximum(X.TAU_F32, 16 * U32 * kappa(ns, poses, I_ref))
+    kap = kappa(ns, poses, I_ref)
+    tau = np.maximum(X.TAU_F32, (2 if comp else 16) * U32 * kap)
     err = X.rel_fro(X.unpack21(fim), I_ref)
+    big = kap > X.TAU_F32 / U32 / 16        # poses whose kappa term exceeds the 1e-5 floor at 16 u
+    print(f"GP query N_s = {ns}, oracle D uploaded, {'compensated' if comp else 'single-precision'} "
+          f"contraction: error max {err.max():.2e} p99 {np.percentile(err, 99):.2e}; kappa median "
+          f"{np.median(kap):.1f} p99 {np.percentile(kap, 99):.1f} max {kap.max():.1f}; error / (u kappa) max "
+          f"{(err / (U32 * kap)).max():.2f}, over the {int(big.sum())} poses with kappa > {X.TAU_F32 / U32 / 16:.0f}: "
+          f"{(err[big] / (U32 * kap[big])).max() if big.any() else 0:.2f}")
     assert np.all(err <= tau), (err.max(), (err / tau).max())
     assert np.median(err) <= X.TAU_F32
     check_metrics(I_ref, met, sg, tau)
