@@ -300,9 +300,10 @@ FIF_API int32_t fif_build_static(fif_field* field, const float* d_landmarks, int
  *   d_metrics  float64[m][3]   trace, log|det|, lambda_min (unselected columns untouched)
  *   d_sign     int8[m]         sign of det (+1, -1, 0)
  *   d_status   int32[m]        FIF_POSE_* bits
- * Trace is summed in single precision; log|det| comes from a double-precision LDL^T
- * (LU with pivoting when it breaks down) of the FIM, and lambda_min from a
- * single-precision Jacobi eigenvector refined by a double-precision Rayleigh quotient.
+ * Trace is summed in single precision; log|det| comes from a double-precision LU with partial
+ * pivoting of the FIM, and lambda_min is the double-precision Rayleigh quotient of the eigenvector
+ * that single-precision inverse iteration finds (its shift from bisection on the Sturm counts of
+ * a Householder tridiagonal form).
  * Positions outside the lattice are clamped onto it.  m = 0 returns FIF_OK and touches nothing
  * (every pointer may then be NULL).
  * GP field (FIF_STORAGE_GP): I(T) = sum_g a_g(z) D_g(t) with the kriging weights

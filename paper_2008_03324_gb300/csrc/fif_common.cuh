@@ -218,99 +218,161 @@ FIF_DEV void logdet_f64(const float* s, double& logabs, int& sign) {
 }
 
 // ---- smallest eigenvalue ------------------------------------------------------------
-// Jacobi rotation (t = tan, c = cos, s = sin) that zeroes a_pq of a symmetric 2x2 block,
-// with the convention a'_rp = c a_rp - s a_rq, a'_rq = s a_rp + c a_rq.  Fast intrinsics:
-// the angle only has to reduce the off-diagonal mass, not be correctly rounded.
-FIF_DEV void jacobi_angle(float app, float aqq, float apq, float& t, float& c, float& s) {
-    const float theta = __fdividef(aqq - app, 2.f * apq);
-    const float h = fmaf(theta, theta, 1.f);
-    const float root = h * rsqrtf(h);
-    float tt = copysignf(__fdividef(1.f, fabsf(theta) + root), theta);
-    const bool skip = !(fabsf(apq) > 1e-30f * (fabsf(app) + fabsf(aqq))) || !isfinite(tt);
-    tt = skip ? 0.f : tt;
-    t = tt;
-    c = rsqrtf(fmaf(tt, tt, 1.f));
-    s = tt * c;
-}
-
-// One round of the parallel (Brent-Luk) ordering for n = 6: three rotations on disjoint index
-// pairs, whose angles all come from the current matrix, applied together as A <- J^T A J,
-// V <- V J.  Three independent dependency chains per round instead of one.
-template <int p0, int q0, int p1, int q1, int p2, int q2>
-FIF_DEV void jacobi_round(float (&a)[6][6], float (&V)[6][6]) {
-    constexpr int P[3] = {p0, p1, p2}, Q[3] = {q0, q1, q2};
-    float t[3], c[3], s[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) jacobi_angle(a[P[k]][P[k]], a[Q[k]][Q[k]], a[P[k]][Q[k]], t[k], c[k], s[k]);
-    // blocks between two different pairs: X' = J_k^T X J_l
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-        for (int l = k + 1; l < 3; ++l) {
-            const int p = P[k], q = Q[k], u = P[l], v = Q[l];
-            // columns (pair l)
-            const float xpu = c[l] * a[p][u] - s[l] * a[p][v], xpv = s[l] * a[p][u] + c[l] * a[p][v];
-            const float xqu = c[l] * a[q][u] - s[l] * a[q][v], xqv = s[l] * a[q][u] + c[l] * a[q][v];
-            // rows (pair k)
-            const float ypu = c[k] * xpu - s[k] * xqu, yqu = s[k] * xpu + c[k] * xqu;
-            const float ypv = c[k] * xpv - s[k] * xqv, yqv = s[k] * xpv + c[k] * xqv;
-            a[p][u] = a[u][p] = ypu;
-            a[p][v] = a[v][p] = ypv;
-            a[q][u] = a[u][q] = yqu;
-            a[q][v] = a[v][q] = yqv;
-        }
-    // diagonal blocks
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const int p = P[k], q = Q[k];
-        const float apq = a[p][q];
-        a[p][p] = a[p][p] - t[k] * apq;
-        a[q][q] = a[q][q] + t[k] * apq;
-        a[p][q] = a[q][p] = 0.f;
-    }
-#pragma unroll
-    for (int r = 0; r < 6; ++r)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const float vp = V[r][P[k]], vq = V[r][Q[k]];
-            V[r][P[k]] = c[k] * vp - s[k] * vq;
-            V[r][Q[k]] = s[k] * vp + c[k] * vq;
-        }
-}
-
-// Smallest eigenvalue of a symmetric 6x6 (packed, float): parallel-ordered Jacobi in single
-// precision gives the eigenvector x of the smallest diagonal; the eigenvalue is the Rayleigh
-// quotient x^T S x / x^T x in double precision (its error is second order in the error of x).
-// If xout is given, x (unit, float) is returned too.
-template <int SWEEPS = 4>
+// Smallest eigenvalue of a symmetric 6x6 (packed, float).  Householder reduction to tridiagonal
+// form T in single precision (Golub and Van Loan, Sec. 8.3.1); bisection on Sturm counts of T (the
+// number of negative pivots of the LDL^T factorisation of T - sigma I is the number of eigenvalues
+// below sigma, Golub and Van Loan, Sec. 8.4.1) to single-precision resolution gives the shift mu;
+// three steps of inverse iteration with S - mu I on the original matrix give the eigenvector x;
+// the eigenvalue is the Rayleigh quotient x^T S x / x^T x in double precision on the original
+// matrix, whose error is second order in the error of x.  If xout is given, x (unit, float) is
+// returned too.
 FIF_DEV double lambda_min_f64(const float* s, float* xout = nullptr) {
-    float a[6][6], V[6][6];
+    float a[6][6];
 #pragma unroll
     for (int r = 0; r < 6; ++r)
 #pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            a[r][c] = s[sym_idx(r, c)];
-            V[r][c] = (r == c) ? 1.f : 0.f;
+        for (int c = 0; c < 6; ++c) a[r][c] = s[sym_idx(r, c)];
+    // reflections H_k = I - beta_k v_k v_k^T acting on rows / columns k+1..5, v_k kept in
+    // a[k+1..5][k]; the lower triangle of the trailing block holds the reduced matrix
+    float e[5], d[6];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float nrm2 = 0.f;
+#pragma unroll
+        for (int i = k + 1; i < 6; ++i) nrm2 = fmaf(a[i][k], a[i][k], nrm2);
+        const float x0 = a[k + 1][k];
+        const float nrm = sqrtf(nrm2);
+        const float alpha = x0 >= 0.f ? -nrm : nrm;
+        const float v0 = x0 - alpha;
+        const float vv = fmaf(v0, v0, nrm2 - x0 * x0);
+        const bool skip = !(vv > 0.f);
+        const float beta = skip ? 0.f : 2.f / vv;
+        a[k + 1][k] = v0;
+        e[k] = skip ? x0 : alpha;
+        // trailing block B (rows / columns k+1..5): B <- H B H
+        float p[6], K = 0.f;
+#pragma unroll
+        for (int i = k + 1; i < 6; ++i) {
+            float t = 0.f;
+#pragma unroll
+            for (int j = k + 1; j < 6; ++j) t = fmaf(a[i > j ? i : j][i > j ? j : i], a[j][k], t);
+            p[i] = beta * t;
+            K = fmaf(p[i], a[i][k], K);
         }
-#pragma unroll 1
-    for (int sweep = 0; sweep < SWEEPS; ++sweep) {
-        jacobi_round<0, 1, 2, 3, 4, 5>(a, V);
-        jacobi_round<0, 2, 1, 4, 3, 5>(a, V);
-        jacobi_round<0, 3, 1, 5, 2, 4>(a, V);
-        jacobi_round<0, 4, 1, 3, 2, 5>(a, V);
-        jacobi_round<0, 5, 1, 2, 3, 4>(a, V);
+        K *= 0.5f * beta;
+#pragma unroll
+        for (int i = k + 1; i < 6; ++i) p[i] = fmaf(-K, a[i][k], p[i]);
+#pragma unroll
+        for (int i = k + 1; i < 6; ++i)
+#pragma unroll
+            for (int j = k + 1; j <= i; ++j) a[i][j] = a[i][j] - a[i][k] * p[j] - p[i] * a[j][k];
     }
-    float best = a[0][0];
+    e[4] = a[5][4];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) d[i] = a[i][i];
+    float e2[5], lo = d[0], hi = d[0], scale = fabsf(d[0]);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) e2[i] = e[i] * e[i];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const float ri = (i > 0 ? fabsf(e[i - 1]) : 0.f) + (i < 5 ? fabsf(e[i]) : 0.f);
+        lo = fminf(lo, d[i] - ri);
+        hi = fminf(hi, d[i]);
+        scale = fmaxf(scale, fabsf(d[i]) + ri);
+    }
+    const float pivmin = fmaxf(scale * 1e-30f, 1e-37f);
+    // number of eigenvalues below sigma
+    auto below = [&](float sigma) {
+        int cnt = 0;
+        float q = d[0] - sigma;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            if (i > 0) q = (d[i] - sigma) - __fdividef(e2[i - 1], q);
+            q = fabsf(q) < pivmin ? -pivmin : q;
+            cnt += q < 0.f ? 1 : 0;
+        }
+        return cnt;
+    };
+    // lambda_min in [lo, hi]: lo is a Gershgorin bound, hi the smallest diagonal entry
+#pragma unroll 1
+    for (int it = 0; it < 26; ++it) {
+        const float mid = 0.5f * (lo + hi);
+        if (below(mid) >= 1) hi = mid;
+        else lo = mid;
+    }
+    const float mu = 0.5f * (lo + hi);
+    // the eigenvector: three steps of inverse iteration with S - mu I on the original matrix
+    // (single-precision LU with partial pivoting; a pivot below 2^-22 of the scale is raised to it)
+    float b[6][6];
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) b[r][c] = s[sym_idx(r, c)] - (r == c ? mu : 0.f);
+    const float tiny = fmaxf(scale * 2.384185791015625e-7f, 1e-30f);
+    int pv[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        int p = c;
+        float best = fabsf(b[c][c]);
+#pragma unroll
+        for (int r = c + 1; r < 6; ++r) {
+            const float v = fabsf(b[r][c]);
+            if (v > best) { best = v; p = r; }
+        }
+        pv[c] = p;
+#pragma unroll
+        for (int r = c + 1; r < 6; ++r) {
+            const bool sw = (r == p);
+#pragma unroll
+            for (int j = 0; j < 6; ++j) {
+                const float u = b[c][j], w = b[r][j];
+                b[c][j] = sw ? w : u;
+                b[r][j] = sw ? u : w;
+            }
+        }
+        float dd = b[c][c];
+        dd = fabsf(dd) < tiny ? (dd < 0.f ? -tiny : tiny) : dd;
+        b[c][c] = dd;
+        const float inv = __frcp_rn(dd);
+#pragma unroll
+        for (int r = c + 1; r < 6; ++r) {
+            const float f = b[r][c] * inv;
+            b[r][c] = f;
+#pragma unroll
+            for (int j = c + 1; j < 6; ++j) b[r][j] = fmaf(-f, b[c][j], b[r][j]);
+        }
+    }
     float x[6];
 #pragma unroll
-    for (int r = 0; r < 6; ++r) x[r] = V[r][0];
+    for (int r = 0; r < 6; ++r) x[r] = 1.f;
 #pragma unroll
-    for (int c = 1; c < 6; ++c) {
-        const float d = a[c][c];
-        const bool take = d < best;
-        best = take ? d : best;
+    for (int step = 0; step < 3; ++step) {
 #pragma unroll
-        for (int r = 0; r < 6; ++r) x[r] = take ? V[r][c] : x[r];
+        for (int c = 0; c < 6; ++c)
+#pragma unroll
+            for (int r = c + 1; r < 6; ++r) {
+                const bool sw = (r == pv[c]);
+                const float u = x[c], w = x[r];
+                x[c] = sw ? w : u;
+                x[r] = sw ? u : w;
+            }
+#pragma unroll
+        for (int r = 1; r < 6; ++r)
+#pragma unroll
+            for (int c = 0; c < r; ++c) x[r] = fmaf(-b[r][c], x[c], x[r]);
+#pragma unroll
+        for (int r = 5; r >= 0; --r) {
+            float v = x[r];
+#pragma unroll
+            for (int c = r + 1; c < 6; ++c) v = fmaf(-b[r][c], x[c], v);
+            x[r] = __fdividef(v, b[r][r]);
+        }
+        float mx = 0.f;
+#pragma unroll
+        for (int r = 0; r < 6; ++r) mx = fmaxf(mx, fabsf(x[r]));
+        const float inv = mx > 0.f ? __frcp_rn(mx) : 1.f;
+#pragma unroll
+        for (int r = 0; r < 6; ++r) x[r] *= inv;
     }
     double xd[6], num = 0.0, den = 0.0;
 #pragma unroll

@@ -517,7 +517,7 @@ int launch_query_cfg(const QueryArgs& a, cudaStream_t stream) {
 }
 
 int launch_query(const QueryArgs& a, cudaStream_t stream) {
-    if (a.storage == FIF_STORAGE_BF16) return launch_query_cfg<2, 8, 4, 3, 4>(a, stream);
+    if (a.storage == FIF_STORAGE_BF16) return launch_query_cfg<2, 8, 8, 3, 2>(a, stream);
     return launch_query_cfg<4, kGather, kMetric, kStages, kPrefetch>(a, stream);
 }
 
