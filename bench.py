@@ -50,18 +50,22 @@ BF16_QUERY_BYTES_PER_POSE = 8 * 210 * 2
 TRACE_QUERY_BYTES_PER_POSE = 8 * 10 * 4
 # shell test 8, rsqrt 1, bearing and 1/n^2 4, products 26, 66 accumulations (46 FMA, 20 FADD) 112
 BUILD_FLOPS_PER_PAIR = 151
-# DRAM traffic of one query launch per pose, from one ncu capture of query_kernel on the bench's
-# 2^22-pose step (read 29.017 GB + write 0.475 GB for 4,194,304 poses; summary under profiles/),
-# valid while the kernel sources hash to the recorded digest
-QUERY_TRAFFIC = {"bytes_per_pose": (29.016678e9 + 0.475145e9) / 4194304,
-                 "digest": "cd3b4e4e7a2dfbb8"}
-# the same for the GP query (N_s = 70), captured on the 200 x 200 x 8 lattice (read 11.724 GB +
-# write 0.0118 GB for 262,144 poses)
-GP_QUERY_TRAFFIC = {"bytes_per_pose": (11.723970e9 + 0.011759e9) / 262144, "n_samples": 70,
-                    "digest": "74ef5490899859da"}
+# DRAM traffic of one query launch per pose, from one ncu capture of query_kernel on a 2^20-pose
+# launch over the full warehouse field (read 7.254 GB + write 0.118 GB; traffic per pose does not
+# depend on the batch for uniform-random poses; summary under profiles/), valid while the kernel
+# sources hash to the recorded digest
+QUERY_TRAFFIC = {"bytes_per_pose": (7.253583360e9 + 0.117604864e9) / 1048576,
+                 "digest": "d358181d04697a04"}
+# the same for the GP query (N_s = 70), captured on the 200 x 200 x 8 lattice (read 11.722 GB +
+# write 0.0121 GB for 262,144 poses)
+GP_QUERY_TRAFFIC = {"bytes_per_pose": (11.722481664e9 + 0.0121088e9) / 262144, "n_samples": 70,
+                    "digest": "7f9443fb3d59c90d"}
 # FMA-pipe utilisation of build_kernel (ncu sm__pipe_fma_cycles_active on the 200 x 200 x 8
 # lattice), valid while the build sources hash to the recorded digest
-BUILD_PIPE = {"fma_pipe_active": 0.679, "digest": "598e801891ee396e"}
+BUILD_PIPE = {"fma_pipe_active": 0.731, "digest": "e4ce5491cb7ea36c"}
+# thread instructions per pose-landmark pair of pointcloud_kernel (ncu smsp__inst_executed x 32 /
+# pairs on one full-wave launch over the 200,000 warehouse landmarks)
+PC_INSTRUCTIONS = {"per_pair": 37996388146 * 32 / (77824 * 200000), "digest": "b4e6417eb0a394a0"}
 # GP build, per (in-shell pair, sample axis): sigmoid 10 (dot 6, shift 1, exp 1, add 1, rcp 1)
 # + 15 moment accumulations 30; per pair: bearing products 16
 GP_FLOPS_PER_PAIR_SAMPLE = 40
@@ -416,10 +420,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--poses", type=int, default=1 << 22)
-    ap.add_argument("--phase", default="all", choices=["all", "query", "build", "gp"],
+    ap.add_argument("--phase", default="all", choices=["all", "query", "build", "gp", "pointcloud"],
                     help="build: time only the build; query: build once untimed, time only the query; "
                          "gp: only the GP-visibility field block")
     ap.add_argument("--gp-samples", type=int, default=70, help="GP sample axes N_s of the GP block")
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16"],
+                    help="field storage of the query phase (the full run times float32 first)")
     ap.add_argument("--build-nz", type=int, default=40, help="lattice z-layers (smaller for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 2M-landmark building map")
@@ -462,7 +468,19 @@ def main():
                               "n_gpus": ws, "config": {"workload": WORKLOAD, "lattice": list(spec.dims)},
                               "gp": gpo}), flush=True)
         return 0
-    field = fif.Field(spec.origin, spec.res, spec.dims, params)
+    if args.phase == "pointcloud":
+        # the point-cloud baseline alone: one full-wave launch over all landmarks per step
+        pposes = torch.from_numpy(synth.random_poses(1000 + rank, PC_POSES, spec.lo, spec.hi)).to(dev)
+        pmet = torch.empty(PC_POSES, 3, dtype=torch.float64, device=dev)
+        tp = time_events(lambda: fif.pointcloud_fim(lm, params, fif.make_pinhole(), pposes, fif.Q_METRICS, None, pmet,
+                                                    None, None), max(1, args.steps), args.warmup, stream)
+        if rank == 0:
+            print(json.dumps({"metric": "point-cloud FIM poses/s", "unit": "queries/s",
+                              "value": PC_POSES / (float(np.mean(tp)) * 1e-3), "kernel_ms": float(np.mean(tp)),
+                              "poses": PC_POSES, "landmarks": int(lm.shape[0])}), flush=True)
+        return 0
+    query_storage = fif.STORAGE_BF16 if (args.phase == "query" and args.storage == "bf16") else fif.STORAGE_F32
+    field = fif.Field(spec.origin, spec.res, spec.dims, params, storage=query_storage)
     wsb = torch.empty(fif.build_workspace_bytes(field.c, lm.shape[0]), dtype=torch.uint8, device=dev)
 
     out = {}
@@ -575,10 +593,12 @@ def main():
     status = st.cpu().numpy()
 
     if args.phase == "query":
+        if query_storage == fif.STORAGE_BF16:
+            achieved = m * BF16_QUERY_BYTES_PER_POSE / (kernel_ms * 1e-3) / 1e9
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws,
                               "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-                              "kernel_ms": kernel_ms, "roofline_achieved_gbs": achieved,
+                              "kernel_ms": kernel_ms, "roofline_achieved_gbs": achieved, "storage": args.storage,
                               "config": {"workload": WORKLOAD, "poses_per_step": m}}), flush=True)
         return 0
 
@@ -626,9 +646,15 @@ def main():
                                                 fim, met, sg, st), 3, 1, stream)
     pc_ms = float(np.mean(tp))
     pc_rate = mp / (pc_ms * 1e-3)
+    pc_pairs_s = mp * int(lm.shape[0]) / (pc_ms * 1e-3)
+    ipp = (PC_INSTRUCTIONS["per_pair"] if PC_INSTRUCTIONS["digest"] ==
+           query_source_digest(("pointcloud.cu", "fif_common.cuh")) else None)
     out["pointcloud"] = {"queries_per_s": pc_rate, "landmarks": int(lm.shape[0]), "poses": mp,
                          "launch": f"{mp} poses = {mp // 128} CTAs of 128 threads (4 per SM on 152 SMs)",
-                         "kernel_ms": pc_ms, "pose_landmark_pairs_per_s": mp * int(lm.shape[0]) / (pc_ms * 1e-3),
+                         "kernel_ms": pc_ms, "pose_landmark_pairs_per_s": pc_pairs_s,
+                         "instructions_per_pair_ncu": ipp,
+                         "issue_rate_fraction": (ipp * pc_pairs_s / (SMS * 4 * 32 * SM_MAX_MHZ * 1e6)
+                                                 if ipp else None),
                          "field_speedup": (value / ws) / pc_rate}
 
     # ---------------- bfloat16 storage (same map, same poses) ----------------

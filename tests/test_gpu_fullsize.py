@@ -59,12 +59,21 @@ def test_warehouse_query_2m22_sampled(F, setup, storage):
     err = X.rel_fro(got, I_ref)
     assert err.max() <= tau, err.max()
     np.testing.assert_array_equal(st[torch.from_numpy(sample).cuda()].cpu().numpy() & 3, st_ref & 3)
+    m = met[torch.from_numpy(sample).cuda()].cpu().numpy()
     if storage == "f32":
         mo = O.metrics(I_ref)
         t_tr, t_lm, _ = X.metric_tolerances(I_ref, tau)
-        m = met[torch.from_numpy(sample).cuda()].cpu().numpy()
         assert np.all(np.abs(m[:, 0] - mo[:, 0]) <= t_tr)
         assert np.all(np.abs(m[:, 2] - mo[:, 3]) <= t_lm)
+    # the metric arithmetic alone, on the FIMs the launch returned (read back as float32 and
+    # evaluated in FP64 by the oracle): lambda_min to 1e-9 ||I||, log|det| to 1e-12 ||I|| ||I^-1||
+    I = got                     # the float32 FIM entries, exact in float64
+    mo = O.metrics(I)
+    n = X.fro(I)
+    inv = np.array([X.fro(np.linalg.pinv(M)) for M in I])
+    assert np.all(np.abs(m[:, 2] - mo[:, 3]) <= 1e-9 * n), np.max(np.abs(m[:, 2] - mo[:, 3]) / n)
+    ok = mo[:, 2] != 0
+    assert np.all(np.abs(m[ok, 1] - mo[ok, 1]) <= 1e-12 * n[ok] * inv[ok] + 5e-7)
 
 
 def test_warehouse_gp_query_2m22_sampled(F, setup):

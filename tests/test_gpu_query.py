@@ -169,8 +169,8 @@ def test_bf16_build_and_query_vs_fp64_oracle(F):
 def test_metrics_of_the_returned_fim(F, storage):
     """The metric arithmetic alone: log|det|, its sign and lambda_min of the FIM the kernel
     returned (read back as float32 and evaluated in FP64 by the oracle) agree to double
-    precision -- log|det| within 1e-12 ||I|| ||I^-1|| + 5e-7, lambda_min within 1e-7 ||I||
-    (single-precision Jacobi eigenvector, double-precision Rayleigh quotient)."""
+    precision -- log|det| within 1e-12 ||I|| ||I^-1|| + 5e-7, lambda_min within 1e-9 ||I||
+    (single-precision inverse iteration for the eigenvector, double-precision Rayleigh quotient)."""
     field = uploaded_room_field(F, storage=storage)
     fim, met, sg, st = run(F, field, X.room_poses(1000))
     I = X.unpack21(fim)
@@ -180,7 +180,7 @@ def test_metrics_of_the_returned_fim(F, storage):
     ok = mo[:, 2] != 0
     assert np.all(np.abs(met[ok, 1] - mo[ok, 1]) <= 1e-12 * n[ok] * inv[ok] + 5e-7)
     np.testing.assert_array_equal(sg[ok], mo[ok, 2].astype(np.int8))
-    assert np.all(np.abs(met[:, 2] - mo[:, 3]) <= 1e-7 * n)
+    assert np.all(np.abs(met[:, 2] - mo[:, 3]) <= 1e-9 * n)
     assert np.all(np.abs(met[:, 0] - np.trace(I, axis1=1, axis2=2)) <= 1e-6 * n)
 
 
