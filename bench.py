@@ -103,7 +103,9 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while active."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms while active.  Entering waits
+    (at most 5 s) for the first sample, so that sampling runs before the work starts; mark() and
+    summary() keep only the samples taken between the marks (the GPU under load)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -113,21 +115,28 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.lines = []
+        self.marks = []
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.monotonic()
+            while not self.lines and self.proc.poll() is None and time.monotonic() - t0 < 5.0:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
+
+    def mark(self):
+        self.marks.append(time.monotonic())
 
     def __exit__(self, *a):
         if self.proc is not None:
@@ -140,7 +149,12 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        # the window between the marks, widened by one sampling period so that a window shorter
+        # than the period still holds the sample taken as it ran
+        lo, hi = (self.marks[0] - 0.1, self.marks[-1] + 0.1) if len(self.marks) >= 2 else (-np.inf, np.inf)
+        for t, ln in self.lines:
+            if not lo <= t <= hi:
+                continue
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -566,6 +580,7 @@ def main():
 
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     with ClockSampler(local) as clk:
+        clk.mark()
         for _ in range(args.warmup):
             qstep()
         torch.cuda.synchronize()
@@ -580,6 +595,7 @@ def main():
             b.record(stream)
         t_all1.record(stream)
         torch.cuda.synchronize()
+        clk.mark()
     dist.barrier()
     torch.cuda.synchronize()
     launches += args.steps
