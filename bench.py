@@ -51,18 +51,18 @@ TRACE_QUERY_BYTES_PER_POSE = 8 * 10 * 4
 # shell test 8, rsqrt 1, bearing and 1/n^2 4, products 26, 66 accumulations (46 FMA, 20 FADD) 112
 BUILD_FLOPS_PER_PAIR = 151
 # DRAM traffic of one query launch per pose, from one ncu capture of query_kernel on a 2^20-pose
-# launch over the full warehouse field (read 7.254 GB + write 0.118 GB; traffic per pose does not
+# launch over the full warehouse field (read 7.252 GB + write 0.118 GB; traffic per pose does not
 # depend on the batch for uniform-random poses; summary under profiles/), valid while the kernel
 # sources hash to the recorded digest
-QUERY_TRAFFIC = {"bytes_per_pose": (7.253583360e9 + 0.117604864e9) / 1048576,
-                 "digest": "d358181d04697a04"}
+QUERY_TRAFFIC = {"bytes_per_pose": (7.252397312e9 + 0.117576192e9) / 1048576,
+                 "digest": "69816fa714c909c4"}
 # the same for the GP query (N_s = 70), captured on the 200 x 200 x 8 lattice (read 11.722 GB +
 # write 0.0121 GB for 262,144 poses)
 GP_QUERY_TRAFFIC = {"bytes_per_pose": (11.722481664e9 + 0.0121088e9) / 262144, "n_samples": 70,
                     "digest": "7f9443fb3d59c90d"}
 # FMA-pipe utilisation of build_kernel (ncu sm__pipe_fma_cycles_active on the 200 x 200 x 8
 # lattice), valid while the build sources hash to the recorded digest
-BUILD_PIPE = {"fma_pipe_active": 0.731, "digest": "e4ce5491cb7ea36c"}
+BUILD_PIPE = {"fma_pipe_active": 0.732, "digest": "868ff3fdea8c5974"}
 # thread instructions per pose-landmark pair of pointcloud_kernel (ncu smsp__inst_executed x 32 /
 # pairs on one full-wave launch over the 200,000 warehouse landmarks)
 PC_INSTRUCTIONS = {"per_pair": 37996388146 * 32 / (77824 * 200000), "digest": "b4e6417eb0a394a0"}

@@ -69,7 +69,8 @@ typedef struct CUstream_st* fif_stream_t;
 
 /* ---- storage of the field ------------------------------------------------------------ */
 #define FIF_STORAGE_F32 0    /* float32, 216 elements (864 B) per node                  */
-#define FIF_STORAGE_BF16 1   /* bfloat16 (round to nearest even), 224 elements (448 B)    */
+#define FIF_STORAGE_BF16 1   /* bfloat16 (round to nearest even), 224 elements (448 B),   */
+                             /* monomial blocks of 22 elements (see fif_field)            */
 #define FIF_STORAGE_GP 3     /* GP visibility (Sec. V-B-2): float32, per node the 21 x N_s  */
                              /* matrix of D_g (see fif_gp), entry e of D_g at e*rs + g with  */
                              /* rs = fif_gp_row_stride(N_s); fif_gp_stride(N_s) per node     */
@@ -159,7 +160,9 @@ typedef struct fif_gp {
  * from the node to landmark i, I_i its information (Eq. global_fim_eq) with the
  * rotational part of the perturbation taken about the node itself (the paper's world
  * frame moved to the node: C^world = M_c^T C M_c, M_c = [[I, -[c]x], [0, I]]).
- * Elements 210 .. stride-1 are zero.  With FIF_STORAGE_TRACE, node n holds instead the 10 traces
+ * Elements 210 .. stride-1 are zero.  FIF_STORAGE_BF16 spaces the blocks by 22 instead: entry e
+ * of C_k at n*stride + 22*k + e, with zeros at 22*k + 21 and at 220 .. 223 (so that a 32-bit word
+ * holds two entries of one block).  With FIF_STORAGE_TRACE, node n holds instead the 10 traces
  * tr(C_k^world) (world frame: rotation about the origin) at n*12 + k, then two zeros.
  * k[] = (k0, k1, k2) is filled by fif_field_init. */
 typedef struct fif_field {

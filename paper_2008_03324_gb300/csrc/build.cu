@@ -291,7 +291,13 @@ FIF_DEV void store_f32(float4* dst, const float (&m)[kMom], float scale, int acc
      ...);
 }
 
-// bfloat16 storage: element O of the node record (stride 224)
+// bfloat16 storage: element O of the node record (stride 224; monomial blocks of 22 elements,
+// entry 21 of each block and elements 220..223 zero)
+template <int O>
+FIF_DEV float coef_bf16(const float (&m)[kMom]) {
+    if constexpr (O >= 220 || O % 22 == 21) return 0.f;
+    else return coef_of<(O / 22) * 21 + O % 22>(m);
+}
 template <int... O>
 FIF_DEV void store_bf16(__nv_bfloat16* dst, const float (&m)[kMom], float scale, int acc,
                         std::integer_sequence<int, O...>) {
@@ -299,7 +305,7 @@ FIF_DEV void store_bf16(__nv_bfloat16* dst, const float (&m)[kMom], float scale,
         if (acc != 0) v = fmaf((float)acc, v, __bfloat162float(*d));
         *d = __float2bfloat16_rn(v);
     };
-    (one(dst + O, coef_of<O>(m) * scale), ...);
+    (one(dst + O, coef_bf16<O>(m) * scale), ...);
 }
 
 // the 21 entries of C_k (times scale)

@@ -15,7 +15,7 @@ namespace {
 // first bounded-wait failure seen by any kernel on this device (per device copy)
 __device__ int g_device_error = 0;
 
-constexpr int32_t kVersion = 10000;  // 1.0.0
+constexpr int32_t kVersion = 10100;  // 1.1.0: bfloat16 records in monomial blocks of 22
 constexpr uint64_t kDefaultWaitNs = 2000000000ull;   // 2 s
 // limit of every bounded device wait in the kernels launched from now on (fif_set_wait_limit)
 std::atomic<uint64_t> g_wait_ns{kDefaultWaitNs};

@@ -23,18 +23,22 @@ struct Layout;
 template <>
 struct Layout<4> {
     static constexpr int kStride = 216;                 // floats per node
+    static constexpr int kBlock = 21;                   // elements per monomial block
     static constexpr int kNodeBytes = kStride * 4;      // 864
     static constexpr int kPairBytes = 2 * kNodeBytes;   // 1728
     static constexpr int kPoseBytes = 7296;             // 57 * 128
     __device__ static constexpr int slot(int P) { return P * 1792 + (P == 0 ? 0 : P == 1 ? 16 : P == 2 ? 64 : 80); }
     __device__ static float load(const unsigned char* p, int idx) { return reinterpret_cast<const float*>(p)[idx]; }
 };
-// bfloat16 storage: 224 elements (448 B) per node, pair 896 B; the corners of pair P start at
-// residues 16 P and 16 P + 64 modulo 128 B, so the 8 corners occupy distinct 16-B bank groups
-// and a lane's 4 consecutive 2-byte entries (at most 3 words) never collide with another corner
+// bfloat16 storage: 224 elements (448 B) per node, pair 896 B; monomial block k holds its 21
+// entries at 22 k + e and a zero at 22 k + 21 (elements 220..223 zero), so 32-bit word 11 k + p
+// holds entries 2p and 2p + 1 of block k.  The corners of pair P start at residues 16 P and
+// 16 P + 64 modulo 128 B, so the 8 corners occupy distinct 4-bank groups and the 4 lanes of a
+// corner, reading 4 consecutive words, never collide with another corner
 template <>
 struct Layout<2> {
     static constexpr int kStride = 224;
+    static constexpr int kBlock = 22;                   // elements per monomial block
     static constexpr int kNodeBytes = kStride * 2;      // 448
     static constexpr int kPairBytes = 2 * kNodeBytes;   // 896
     static constexpr int kPoseBytes = 4096;

@@ -6,18 +6,23 @@
 // camera frame and reduced to trace / log|det| / lambda_min (Sec. IV).
 //
 // Design (one warp owns a group of 32 poses):
-//  P  lane = pose: cell lookup, trilinear weights, v_r(z), status -> per-pose table (smem).
+//  P  lane = pose: cell lookup, trilinear weights, v_r(z), status -> per-pose table (smem,
+//     columns by pose so that the 32 lanes write distinct banks): the base node's address,
+//     the 8 corner weights w_j and v_r(z) duplicated for the packed FMAs.
 //  G  for each pose of the group the warp gathers the 8 corner coefficient sets
 //     (4 x-adjacent node pairs, 4 bulk copies of 1728 B, triple-buffered through shared
 //     memory, plus an L2 bulk prefetch a few poses ahead).  lane = (corner j, quarter q):
-//     the lane contracts its corner over the 10 monomials for the entries e = q mod 4,
+//     the lane contracts its corner over the 10 monomials for the entries e = q mod 4
+//     (bfloat16 storage: the entry pairs 2p, 2p + 1 with p = q mod 4, one 32-bit word per
+//     pair and monomial, contracted with packed f32x2 FMAs),
 //     weights by w_j, and a 3-level shuffle butterfly over the corner bits turns the 8
 //     corners into the superset sums sum_{j' >= m} w_j' S_j' that the exact change of the
 //     rotational reference point needs (see finalize()).  No lane ever needs a whole
 //     6x6, so there is no per-corner shift and no full reduction.
 //  F  lane = pose: assemble T (about the base node), move it to the camera position,
 //     rotate into the camera frame, write the FIM, then the metrics (FP32 trace, FP64 LU
-//     log|det|, FP32 Jacobi + FP64 Rayleigh lambda_min).
+//     log|det|, lambda_min from a Sturm-bisection shift, inverse iteration and the FP64
+//     Rayleigh quotient).
 #include "fif_common.cuh"
 #include "fif_internal.h"
 #include "gather.cuh"
@@ -28,11 +33,12 @@ namespace {
 
 using namespace gather;
 
-struct PoseEntry {      // 64 B
-    int32_t base_lo, base_hi;
-    float w[3];
-    float vr[10];
-    uint32_t status;
+// per-pose table of a group of 32 poses, written by lane = pose (conflict-free rows) and read
+// by the whole warp for one pose at a time
+struct PoseTable {
+    const char* src[32];     // the base node's record
+    float2 vr2[10][32];      // v_r(z)[k] twice (the operand of a packed FMA)
+    float wj[32][9];         // trilinear weight of corner j (bits x, y, z of j); odd row stride
 };
 
 // moment slot for entry e held by corner-lane j (-1 if that superset sum is not needed)
@@ -79,7 +85,7 @@ constexpr int kSlotFloats = 32 * kRow;
 template <int kElem, int NS>
 struct GatherSmem {
     unsigned char stage[NS][Layout<kElem>::kPoseBytes];
-    PoseEntry ptab[32];
+    PoseTable pt;
     float mom[kMomStride];
     float slot[2][kSlotFloats];
     uint64_t bars[NS];
@@ -201,11 +207,11 @@ __global__ void __launch_bounds__((NG + NM) * 32, 1) query_kernel(QueryArgs args
         // =============================== gather warp ===============================
         GS& G = *reinterpret_cast<GS*>(smem_raw + warp * kGB);
         const int j = lane >> 2, q = lane & 3;
-        const int bx = j & 1, by = (j >> 1) & 1, bz = (j >> 2) & 1;
+        const int bx = j & 1;
         int mslot[6];
 #pragma unroll
         for (int ii = 0; ii < 6; ++ii) {
-            const int e = q + 4 * ii;
+            const int e = (kElem == 2) ? 2 * (q + 4 * (ii >> 1)) + (ii & 1) : q + 4 * ii;
             mslot[ii] = (e < 21) ? mom_slot(e, j) : -1;
         }
         const int corner_off = L::slot(j >> 1) + bx * L::kNodeBytes;
@@ -219,9 +225,8 @@ __global__ void __launch_bounds__((NG + NM) * 32, 1) query_kernel(QueryArgs args
         }
         const int64_t nx = args.nx, nxy = (int64_t)args.nx * args.ny;
         const char* coeffs = reinterpret_cast<const char*>(args.coeffs);
-        auto pair_src = [&](int64_t base, int pp) -> const void* {
-            return coeffs + (base + (pp & 1) * nx + (pp >> 1) * nxy) * (int64_t)L::kNodeBytes;
-        };
+        // byte offset of my node pair (lanes 0..3: pairs (y, z) = (0, 0), (1, 0), (0, 1), (1, 1))
+        const int64_t pair_off = ((lane & 1) * nx + ((lane >> 1) & 1) * nxy) * (int64_t)L::kNodeBytes;
         uint32_t phase_bits = 0;
         int k = 0;
         for (int64_t g = (int64_t)blockIdx.x * kGather + warp; g < groups; g += ngather, ++k) {
@@ -287,13 +292,13 @@ __global__ void __launch_bounds__((NG + NM) * 32, 1) query_kernel(QueryArgs args
                     for (int kk = 0; kk < 10; ++kk) vr[kk] = 0.f;
                 }
                 const int64_t base = i0[0] + nx * i0[1] + nxy * i0[2];
-                PoseEntry& pe = G.ptab[lane];
-                pe.base_lo = (int32_t)(base & 0xffffffff);
-                pe.base_hi = (int32_t)(base >> 32);
-                pe.w[0] = w[0]; pe.w[1] = w[1]; pe.w[2] = w[2];
+                G.pt.src[lane] = coeffs + base * (int64_t)L::kNodeBytes;
 #pragma unroll
-                for (int kk = 0; kk < 10; ++kk) pe.vr[kk] = vr[kk];
-                pe.status = st;
+                for (int jj = 0; jj < 8; ++jj)
+                    G.pt.wj[lane][jj] = ((jj & 1) ? w[0] : 1.f - w[0]) * ((jj & 2) ? w[1] : 1.f - w[1]) *
+                                        ((jj & 4) ? w[2] : 1.f - w[2]);
+#pragma unroll
+                for (int kk = 0; kk < 10; ++kk) G.pt.vr2[kk][lane] = make_float2(vr[kk], vr[kk]);
                 float* row = slot + lane * kRow;
 #pragma unroll
                 for (int a = 0; a < 3; ++a) row[21 + a] = t[a];
@@ -305,34 +310,31 @@ __global__ void __launch_bounds__((NG + NM) * 32, 1) query_kernel(QueryArgs args
                 row[31] = __uint_as_float(st);
             }
             __syncwarp();
-            auto base_of = [&](int i) -> int64_t {
-                return (int64_t)(uint32_t)G.ptab[i].base_lo | ((int64_t)G.ptab[i].base_hi << 32);
-            };
+            auto pair_src = [&](int i) -> const void* { return G.pt.src[i] + pair_off; };
             if (lane < 4) {
                 for (int i = 0; i < min(cnt, kPrefetch + kStages - 1); ++i)
-                    bulk_prefetch_l2(pair_src(base_of(i), lane), L::kPairBytes);
+                    bulk_prefetch_l2(pair_src(i), L::kPairBytes);
                 fence_proxy_async();
                 for (int i = 0; i < min(cnt, kStages - 1); ++i) {
                     uint64_t* bar = &G.bars[i % kStages];
                     mbar_arrive_expect_tx(bar, L::kPairBytes);
-                    bulk_g2s(G.stage[i % kStages] + L::slot(lane), pair_src(base_of(i), lane), L::kPairBytes, bar);
+                    bulk_g2s(G.stage[i % kStages] + L::slot(lane), pair_src(i), L::kPairBytes, bar);
                 }
             }
             // ---- phase G: warp per pose ----
             bool dead = false;
-            for (int i = 0; i < cnt; ++i) {
-                const int s = i % kStages;
+            int s = 0;                          // stage of pose i
+            int sn = kStages - 1;               // stage of pose i + kStages - 1
+            for (int i = 0; i < cnt; ++i, s = (s == kStages - 1) ? 0 : s + 1, sn = (sn == kStages - 1) ? 0 : sn + 1) {
                 if (lane < 4) {
                     const int inext = i + kStages - 1;
                     if (inext < cnt) {
-                        const int sn = inext % kStages;
                         fence_proxy_async();
                         mbar_arrive_expect_tx(&G.bars[sn], L::kPairBytes);
-                        bulk_g2s(G.stage[sn] + L::slot(lane), pair_src(base_of(inext), lane), L::kPairBytes,
-                                 &G.bars[sn]);
+                        bulk_g2s(G.stage[sn] + L::slot(lane), pair_src(inext), L::kPairBytes, &G.bars[sn]);
                     }
                     const int ipf = i + kStages - 1 + kPrefetch;
-                    if (ipf < cnt) bulk_prefetch_l2(pair_src(base_of(ipf), lane), L::kPairBytes);
+                    if (ipf < cnt) bulk_prefetch_l2(pair_src(ipf), L::kPairBytes);
                 }
                 if (__any_sync(0xffffffffu, !mbar_wait_bounded(&G.bars[s], (phase_bits >> s) & 1u, args.wait_ns))) {
                     set_error(args.err, FIF_ETIMEOUT);
@@ -347,20 +349,42 @@ __global__ void __launch_bounds__((NG + NM) * 32, 1) query_kernel(QueryArgs args
                     break;
                 }
                 phase_bits ^= (1u << s);
-                const PoseEntry& pe = G.ptab[i];
-                const float wj = (bx ? pe.w[0] : 1.f - pe.w[0]) * (by ? pe.w[1] : 1.f - pe.w[1]) *
-                                 (bz ? pe.w[2] : 1.f - pe.w[2]);
-                float vrj[10];
-#pragma unroll
-                for (int kk = 0; kk < 10; ++kk) vrj[kk] = wj * pe.vr[kk];
+                const float wj = G.pt.wj[i][j];
                 const unsigned char* C = G.stage[s] + corner_off;
                 float v[6];
+                if constexpr (kElem == 2) {
+                    // blocks of 22 bfloat16: word kk * 11 + p holds entries 2p (low half) and 2p + 1
+                    const uint32_t* Cw = reinterpret_cast<const uint32_t*>(C) + q;
+                    float2 acc[3];
 #pragma unroll
-                for (int ii = 0; ii < 6; ++ii) {
-                    float acc = 0.f;
+                    for (int pp = 0; pp < 3; ++pp) acc[pp] = make_float2(0.f, 0.f);
 #pragma unroll
-                    for (int kk = 0; kk < 10; ++kk) acc = fmaf(vrj[kk], L::load(C, kk * 21 + 4 * ii + q), acc);
-                    v[ii] = acc;
+                    for (int kk = 0; kk < 10; ++kk) {
+                        const float2 vv = G.pt.vr2[kk][i];
+#pragma unroll
+                        for (int pp = 0; pp < 3; ++pp) {
+                            const uint32_t u = Cw[kk * 11 + 4 * pp];
+                            acc[pp] = fma2(vv, make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u)),
+                                           acc[pp]);
+                        }
+                    }
+#pragma unroll
+                    for (int pp = 0; pp < 3; ++pp) {
+                        const float2 r = mul2(acc[pp], make_float2(wj, wj));
+                        v[2 * pp] = r.x;
+                        v[2 * pp + 1] = r.y;
+                    }
+                } else {
+                    float vrj[10];
+#pragma unroll
+                    for (int kk = 0; kk < 10; ++kk) vrj[kk] = wj * G.pt.vr2[kk][i].x;
+#pragma unroll
+                    for (int ii = 0; ii < 6; ++ii) {
+                        float acc = 0.f;
+#pragma unroll
+                        for (int kk = 0; kk < 10; ++kk) acc = fmaf(vrj[kk], L::load(C, kk * 21 + 4 * ii + q), acc);
+                        v[ii] = acc;
+                    }
                 }
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {

@@ -62,18 +62,25 @@ def block_ratio(got, ref, tau, floor=BLOCK_FLOOR):
     return np.where(den > 0, d / np.where(den > 0, den, 1.0), np.where(d > 0, np.inf, 0.0))
 
 
+# elements per monomial block of a node record: 21 for float32 records (stride 216), 22 for
+# bfloat16 records (stride 224: entry 21 of each block is a zero pad)
+BLOCK = {216: 21, 224: 22}
+
+
 def pack_field(F_local, stride=216):
     """Oracle node-local coefficients [N, 10, 6, 6] -> library layout [N, stride] float32."""
     N = F_local.shape[0]
+    blk = BLOCK[stride]
     out = np.zeros((N, stride), np.float32)
-    out[:, :210] = F_local[:, :, SYM_R, SYM_C].reshape(N, 210).astype(np.float32)
+    out[:, :10 * blk].reshape(N, 10, blk)[:, :, :21] = F_local[:, :, SYM_R, SYM_C].astype(np.float32)
     return out
 
 
 def unpack_field(buf):
-    """Library layout [N, stride] -> [N, 10, 6, 6] float64."""
+    """Library layout [N, stride] (stride 216 or 224) -> [N, 10, 6, 6] float64."""
     buf = np.asarray(buf, dtype=np.float64)
-    return unpack21(buf[:, :210].reshape(-1, 10, 21))
+    blk = BLOCK[buf.shape[1]]
+    return unpack21(buf[:, :10 * blk].reshape(-1, 10, blk)[:, :, :21])
 
 
 # ---------------------------------------------------------------------------

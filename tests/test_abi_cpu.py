@@ -40,7 +40,7 @@ def test_status_strings(F):
     assert F.status_str(0) == "ok"
     assert "wait" in F.status_str(F.ETIMEOUT)
     assert F.status_str(12345) == "unknown status"
-    assert F.lib().fif_version() == 10000
+    assert F.lib().fif_version() == 10100
 
 
 def test_field_bytes_and_init_validation(F):

@@ -21,3 +21,20 @@ def test_block_check_passes_rounding_and_catches_a_small_wrong_block():
     bad[n, k] *= 1.0 + 1e-4          # 10x the bound inside the block
     assert X.rel_fro(bad.reshape(-1, 60, 6), ref.reshape(-1, 60, 6))[n] <= X.TAU_F32
     assert X.block_ratio(bad, ref, X.TAU_F32)[n, k] > 1.0
+
+
+def test_record_layouts_round_trip():
+    """float32 records: entry e of C_k at 21 k + e (stride 216); bfloat16 records: at 22 k + e with
+    zeros at 22 k + 21 and 220..223 (stride 224)."""
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((5, 10, 6, 6))
+    A = A + A.transpose(0, 1, 3, 2)
+    for stride, blk in ((216, 21), (224, 22)):
+        buf = X.pack_field(A, stride)
+        assert buf.shape == (5, stride)
+        np.testing.assert_array_equal(X.unpack_field(buf), A.astype(np.float32).astype(np.float64))
+        k, e = 3, 7                                     # entry 7 = (row 1, col 2)
+        assert buf[2, blk * k + e] == np.float32(A[2, k, 1, 2])
+        assert not buf[:, 10 * blk:].any()
+        if blk == 22:
+            assert not buf[:, 21:220:22].any()

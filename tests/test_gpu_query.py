@@ -141,8 +141,7 @@ def test_bf16_storage_query_exact_arithmetic(F):
     spec = X.ROOM["grid"]
     F_loc = X.round_bf16(X.room_field_oracle(True))
     field = F.Field(spec.origin, spec.res, spec.dims, F.make_params(r_max=8.0), storage=F.STORAGE_BF16)
-    buf = np.zeros((F_loc.shape[0], 224), np.float32)
-    buf[:, :210] = F_loc[:, :, X.SYM_R, X.SYM_C].reshape(-1, 210)
+    buf = X.pack_field(F_loc, 224)
     field.coeffs.copy_(torch.from_numpy(buf).to(torch.bfloat16))
     poses = X.room_poses(1000)
     fim, met, sg, st = run(F, field, poses)
