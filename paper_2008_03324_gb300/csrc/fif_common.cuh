@@ -175,20 +175,21 @@ FIF_DEV void logdet_f64(const float* s, double& logabs, int& sign) {
         // pivot search over rows c..5 (on single-precision magnitudes: the choice only
         // affects stability, and the comparisons stay off the slow double-precision pipe)
         int p = c;
-        float best = fabsf((float)a[c][c]);
+        uint32_t best = (uint32_t)__double2hiint(a[c][c]) & 0x7fffffffu;
 #pragma unroll
         for (int r = 0; r < 6; ++r) {
             if (r <= c) continue;
-            const float v = fabsf((float)a[r][c]);
+            const uint32_t v = (uint32_t)__double2hiint(a[r][c]) & 0x7fffffffu;
             if (v > best) { best = v; p = r; }
         }
-        // exchange rows c and p with selects
+        // exchange rows c and p with selects (the columns left of c are not read again)
 #pragma unroll
         for (int r = 0; r < 6; ++r) {
             if (r <= c) continue;
             const bool sw = (r == p);
 #pragma unroll
             for (int j = 0; j < 6; ++j) {
+                if (j < c) continue;
                 const double x = a[c][j], y = a[r][j];
                 a[c][j] = sw ? y : x;
                 a[r][j] = sw ? x : y;
@@ -197,7 +198,12 @@ FIF_DEV void logdet_f64(const float* s, double& logabs, int& sign) {
         if (p != c) sg = -sg;
         const double piv = a[c][c];
         if (piv == 0.0) zero = true;
-        const double inv = 1.0 / piv;
+        // 1 / piv: hardware approximation refined by two steps of Newton's iteration
+        // x <- x + x (1 - piv x)
+        double inv;
+        asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(inv) : "d"(piv));
+        inv = fma(inv, fma(-piv, inv, 1.0), inv);
+        inv = fma(inv, fma(-piv, inv, 1.0), inv);
         prod *= piv;
 #pragma unroll
         for (int r = 0; r < 6; ++r) {
@@ -280,24 +286,29 @@ FIF_DEV double lambda_min_f64(const float* s, float* xout = nullptr) {
         hi = fminf(hi, d[i]);
         scale = fmaxf(scale, fabsf(d[i]) + ri);
     }
-    const float pivmin = fmaxf(scale * 1e-30f, 1e-37f);
-    // number of eigenvalues below sigma
-    auto below = [&](float sigma) {
-        int cnt = 0;
-        float q = d[0] - sigma;
+    // whether an eigenvalue lies below sigma: a negative pivot of T - sigma I = L D L^T.  A zero
+    // pivot (flushed when subnormal) gives an infinite reciprocal and a next pivot of -inf, which
+    // counts the same eigenvalue; e^2 is at least the smallest normal number, so that 0 * inf
+    // never arises
 #pragma unroll
-        for (int i = 0; i < 6; ++i) {
-            if (i > 0) q = (d[i] - sigma) - __fdividef(e2[i - 1], q);
-            q = fabsf(q) < pivmin ? -pivmin : q;
-            cnt += q < 0.f ? 1 : 0;
+    for (int i = 0; i < 5; ++i) e2[i] = fmaxf(e2[i], 1.17549435e-38f);
+    auto any_below = [&](float sigma) {
+        float q = d[0] - sigma;
+        uint32_t sgn = __float_as_uint(q);
+#pragma unroll
+        for (int i = 1; i < 6; ++i) {
+            float r;
+            asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(q));
+            q = fmaf(-e2[i - 1], r, d[i] - sigma);
+            sgn |= __float_as_uint(q);
         }
-        return cnt;
+        return (sgn >> 31) != 0u;
     };
     // lambda_min in [lo, hi]: lo is a Gershgorin bound, hi the smallest diagonal entry
-#pragma unroll 1
+#pragma unroll 2
     for (int it = 0; it < 26; ++it) {
         const float mid = 0.5f * (lo + hi);
-        if (below(mid) >= 1) hi = mid;
+        if (any_below(mid)) hi = mid;
         else lo = mid;
     }
     const float mu = 0.5f * (lo + hi);
@@ -379,9 +390,9 @@ FIF_DEV double lambda_min_f64(const float* s, float* xout = nullptr) {
     for (int r = 0; r < 6; ++r) xd[r] = (double)x[r];
 #pragma unroll
     for (int r = 0; r < 6; ++r) {
-        double y = 0.0;
+        double y = (double)s[sym_idx(r, r)] * xd[r];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) y = fma((double)s[sym_idx(r, c)], xd[c], y);
+        for (int c = r + 1; c < 6; ++c) y = fma((double)s[sym_idx(r, c)], 2.0 * xd[c], y);
         num = fma(xd[r], y, num);
         den = fma(xd[r], xd[r], den);
     }

@@ -10,8 +10,10 @@
 //     columns by pose so that the 32 lanes write distinct banks): the base node's address,
 //     the 8 corner weights w_j and v_r(z) duplicated for the packed FMAs.
 //  G  for each pose of the group the warp gathers the 8 corner coefficient sets
-//     (4 x-adjacent node pairs, 4 bulk copies of 1728 B, triple-buffered through shared
-//     memory, plus an L2 bulk prefetch a few poses ahead).  lane = (corner j, quarter q):
+//     (4 x-adjacent node pairs, 4 bulk copies of 1728 B (896 B for bfloat16), double-
+//     buffered through shared memory, plus an L2 bulk prefetch of the pose after the next;
+//     float32: 8 gather and 4 metric warps per SM, bfloat16: 10 and 5, so that enough copies
+//     are in flight).  lane = (corner j, quarter q):
 //     the lane contracts its corner over the 10 monomials for the entries e = q mod 4
 //     (bfloat16 storage: the entry pairs 2p, 2p + 1 with p = q mod 4, one 32-bit word per
 //     pair and monomial, contracted with packed f32x2 FMAs),
@@ -75,8 +77,8 @@ __device__ __forceinline__ int mom_slot(int e, int j) {
 // Metric warp m serves gather warps m, m + kMetric, ... (kGather / kMetric of them; two
 // slots each, double-buffered).  Every bounded wait that runs out sets a shared abort flag
 // that all warps of the CTA see, so the CTA leaves as a whole (after draining its copies).
-constexpr int kGather = 6;     // gather warps per CTA of the float32 configuration
-constexpr int kMetric = 6;     // metric warps per CTA of the float32 configuration
+constexpr int kGather = 8;     // gather warps per CTA of the float32 configuration
+constexpr int kMetric = 4;     // metric warps per CTA of the float32 configuration
 constexpr int kRow = 33;              // floats per pose in a slot (odd stride: no bank conflicts)
 // slot row: [0..20] T (about the base node, world axes), [21..23] t, [24..27] q,
 //           [28..30] c0, [31] status bits
@@ -541,8 +543,8 @@ int launch_query_cfg(const QueryArgs& a, cudaStream_t stream) {
 }
 
 int launch_query(const QueryArgs& a, cudaStream_t stream) {
-    if (a.storage == FIF_STORAGE_BF16) return launch_query_cfg<2, 8, 8, 3, 2>(a, stream);
-    return launch_query_cfg<4, kGather, kMetric, kStages, kPrefetch>(a, stream);
+    if (a.storage == FIF_STORAGE_BF16) return launch_query_cfg<2, 10, 5, 2, 1>(a, stream);
+    return launch_query_cfg<4, kGather, kMetric, 2, 1>(a, stream);
 }
 
 }  // namespace fif
