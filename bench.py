@@ -51,21 +51,21 @@ TRACE_QUERY_BYTES_PER_POSE = 8 * 10 * 4
 # shell test 8, rsqrt 1, bearing and 1/n^2 4, products 26, 66 accumulations (46 FMA, 20 FADD) 112
 BUILD_FLOPS_PER_PAIR = 151
 # DRAM traffic of one query launch per pose, from one ncu capture of query_kernel on a 2^20-pose
-# launch over the full warehouse field (read 7.252 GB + write 0.118 GB; traffic per pose does not
+# launch over the full warehouse field (read 7.192 GB + write 0.116 GB; traffic per pose does not
 # depend on the batch for uniform-random poses; summary under profiles/), valid while the kernel
 # sources hash to the recorded digest
-QUERY_TRAFFIC = {"bytes_per_pose": (7.252397312e9 + 0.117576192e9) / 1048576,
-                 "digest": "69816fa714c909c4"}
-# the same for the GP query (N_s = 70), captured on the 200 x 200 x 8 lattice (read 11.722 GB +
-# write 0.0121 GB for 262,144 poses)
-GP_QUERY_TRAFFIC = {"bytes_per_pose": (11.722481664e9 + 0.0121088e9) / 262144, "n_samples": 70,
-                    "digest": "7f9443fb3d59c90d"}
+QUERY_TRAFFIC = {"bytes_per_pose": (7.192380160e9 + 0.115532288e9) / 1048576,
+                 "digest": "278518b7f3a81f4c"}
+# the same for the GP query (N_s = 70), captured on the 200 x 200 x 8 lattice (read 11.720 GB +
+# write 0.0111 GB for 262,144 poses)
+GP_QUERY_TRAFFIC = {"bytes_per_pose": (11.720299264e9 + 0.011119872e9) / 262144, "n_samples": 70,
+                    "digest": "ab6462b5c7319dfe"}
 # FMA-pipe utilisation of build_kernel (ncu sm__pipe_fma_cycles_active on the 200 x 200 x 8
 # lattice), valid while the build sources hash to the recorded digest
-BUILD_PIPE = {"fma_pipe_active": 0.732, "digest": "868ff3fdea8c5974"}
+BUILD_PIPE = {"fma_pipe_active": 0.732, "digest": "807ecbe98429a5e4"}
 # thread instructions per pose-landmark pair of pointcloud_kernel (ncu smsp__inst_executed x 32 /
 # pairs on one full-wave launch over the 200,000 warehouse landmarks)
-PC_INSTRUCTIONS = {"per_pair": 37996388146 * 32 / (77824 * 200000), "digest": "b4e6417eb0a394a0"}
+PC_INSTRUCTIONS = {"per_pair": 38000753042 * 32 / (77824 * 200000), "digest": "5e88b65bf0a71852"}
 # GP build, per (in-shell pair, sample axis): sigmoid 10 (dot 6, shift 1, exp 1, add 1, rcp 1)
 # + 15 moment accumulations 30; per pair: bearing products 16
 GP_FLOPS_PER_PAIR_SAMPLE = 40

@@ -542,8 +542,19 @@ int launch_query_cfg(const QueryArgs& a, cudaStream_t stream) {
     return cudaPeekAtLastError() == cudaSuccess ? FIF_OK : FIF_ECUDA;
 }
 
+// A large batch is bound by the bytes in flight: more gather warps with two stages each.  A
+// small batch (fewer than 4 groups of 32 poses per gather warp of that configuration) is bound
+// by the latency of each warp's poses: fewer gather warps, three stages and a deeper L2 prefetch.
 int launch_query(const QueryArgs& a, cudaStream_t stream) {
-    if (a.storage == FIF_STORAGE_BF16) return launch_query_cfg<2, 10, 5, 2, 1>(a, stream);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t groups = (a.m + 31) / 32;
+    if (a.storage == FIF_STORAGE_BF16) {
+        if (groups < 4 * 10 * (int64_t)sms) return launch_query_cfg<2, 8, 8, 3, 2>(a, stream);
+        return launch_query_cfg<2, 10, 5, 2, 1>(a, stream);
+    }
+    if (groups < 4 * kGather * (int64_t)sms) return launch_query_cfg<4, 6, 6, 3, 4>(a, stream);
     return launch_query_cfg<4, kGather, kMetric, 2, 1>(a, stream);
 }
 
