@@ -54,8 +54,8 @@ BUILD_FLOPS_PER_PAIR = 151
 # launch over the full warehouse field (read 7.192 GB + write 0.116 GB; traffic per pose does not
 # depend on the batch for uniform-random poses; summary under profiles/), valid while the kernel
 # sources hash to the recorded digest
-QUERY_TRAFFIC = {"bytes_per_pose": (7.192380160e9 + 0.115532288e9) / 1048576,
-                 "digest": "278518b7f3a81f4c"}
+QUERY_TRAFFIC = {"bytes_per_pose": (7.192873216e9 + 0.116033280e9) / 1048576,
+                 "digest": "4c1b93af14d6619f"}
 # the same for the GP query (N_s = 70), captured on the 200 x 200 x 8 lattice (read 11.720 GB +
 # write 0.0111 GB for 262,144 poses)
 GP_QUERY_TRAFFIC = {"bytes_per_pose": (11.720299264e9 + 0.011119872e9) / 262144, "n_samples": 70,
