@@ -427,6 +427,34 @@ def serve_arrivals(seed, count, rate):
     return synth.poisson_arrivals(seed, count, rate)
 
 
+def trace_block(fif, spec, lm, params, poses, met, st, wsb, stream, hbm_peak):
+    """The positional trace factor (Sec. VI-A-2): build and world-frame trace query of the poses.
+    Its field (12 floats per node, 77 MB on the warehouse lattice) stays in the 129 MB L2 while
+    the poses stream through, so the query is bound by L2-to-SM sector traffic (8 corners x 64 B
+    of sectors per pose), not by HBM; the fraction of the HBM copy bandwidth is reported for
+    comparison only."""
+    import torch
+    m = poses.shape[0]
+    ftr = fif.Field(spec.origin, spec.res, spec.dims, params, storage=fif.STORAGE_TRACE)
+    ttb = time_events(lambda: fif.build(ftr.c, lm, wsb), 2, 1, stream)
+    ttq = time_events(lambda: fif.query(ftr.c, poses, fif.Q_TRACE | fif.Q_WORLD, None, met, None, st), 10, 3,
+                      stream)
+    btr = TRACE_QUERY_BYTES_PER_POSE
+    tq_ms = float(np.mean(ttq))
+    res = {"field_bytes": ftr.coeffs.numel() * 4, "build_ms": float(np.mean(ttb)),
+           "queries_per_s": m / (tq_ms * 1e-3), "bytes_per_pose": btr,
+           "io_bytes_per_pose": 7 * 4 + 8 + 4, "kernel_ms": tq_ms,
+           "roofline": {"bound": "l2", "achieved": m * btr / (tq_ms * 1e-3) / 1e9,
+                        "peak": hbm_peak, "unit": "GB/s",
+                        "frac": m * btr / (tq_ms * 1e-3) / 1e9 / hbm_peak,
+                        "note": "the trace field fits in L2; frac is against the HBM copy bandwidth, for "
+                                "comparison only (the sector traffic from L2 is 8 x 64 B per pose)",
+                        "l2_sector_gbs": m * 8 * 64 / (tq_ms * 1e-3) / 1e9}}
+    del ftr
+    torch.cuda.empty_cache()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -434,7 +462,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--poses", type=int, default=1 << 22)
-    ap.add_argument("--phase", default="all", choices=["all", "query", "build", "gp", "pointcloud"],
+    ap.add_argument("--phase", default="all", choices=["all", "query", "build", "gp", "pointcloud", "trace"],
                     help="build: time only the build; query: build once untimed, time only the query; "
                          "gp: only the GP-visibility field block")
     ap.add_argument("--gp-samples", type=int, default=70, help="GP sample axes N_s of the GP block")
@@ -481,6 +509,20 @@ def main():
             print(json.dumps({"metric": "GP-field queries/s", "value": gpo["queries_per_s"], "unit": "queries/s",
                               "n_gpus": ws, "config": {"workload": WORKLOAD, "lattice": list(spec.dims)},
                               "gp": gpo}), flush=True)
+        return 0
+    if args.phase == "trace":
+        # the positional trace factor alone: build, then the world-frame trace query of the poses
+        tposes = torch.from_numpy(synth.random_poses(1000 + rank, args.poses, spec.lo, spec.hi)).to(dev)
+        tmet = torch.empty(args.poses, 3, dtype=torch.float64, device=dev)
+        tst = torch.empty(args.poses, dtype=torch.int32, device=dev)
+        tf = fif.Field(spec.origin, spec.res, spec.dims, params, storage=fif.STORAGE_TRACE)
+        tws = torch.empty(fif.build_workspace_bytes(tf.c, lm.shape[0]), dtype=torch.uint8, device=dev)
+        del tf
+        tro = trace_block(fif, spec, lm, params, tposes, tmet, tst, tws, stream, hbm_peak)
+        if rank == 0:
+            print(json.dumps({"metric": "trace-factor queries/s", "value": tro["queries_per_s"], "unit": "queries/s",
+                              "n_gpus": ws, "config": {"workload": WORKLOAD, "lattice": list(spec.dims)},
+                              "trace_field": tro}), flush=True)
         return 0
     if args.phase == "pointcloud":
         # the point-cloud baseline alone: one full-wave launch over all landmarks per step
@@ -686,19 +728,7 @@ def main():
     torch.cuda.empty_cache()
 
     # ---------------- positional trace factor (10 floats per node, world-frame trace) ----------------
-    ftr = fif.Field(spec.origin, spec.res, spec.dims, params, storage=fif.STORAGE_TRACE)
-    ttb = time_events(lambda: fif.build(ftr.c, lm, wsb), 2, 1, stream)
-    ttq = time_events(lambda: fif.query(ftr.c, poses, fif.Q_TRACE | fif.Q_WORLD, None, met, None, st), 10, 3,
-                      stream)
-    btr = TRACE_QUERY_BYTES_PER_POSE
-    tq_ms = float(np.mean(ttq))
-    out["trace_field"] = {"field_bytes": ftr.coeffs.numel() * 4, "build_ms": float(np.mean(ttb)),
-                          "queries_per_s": m / (tq_ms * 1e-3), "bytes_per_pose": btr,
-                          "io_bytes_per_pose": 7 * 4 + 8 + 4, "kernel_ms": tq_ms,
-                          "roofline": {"bound": "hbm", "achieved": m * btr / (tq_ms * 1e-3) / 1e9,
-                                       "peak": hbm_peak, "unit": "GB/s",
-                                       "frac": m * btr / (tq_ms * 1e-3) / 1e9 / hbm_peak}}
-    del ftr
+    out["trace_field"] = trace_block(fif, spec, lm, params, poses, met, st, wsb, stream, hbm_peak)
 
     # ---------------- GP visibility field (N_s = 70, the paper's choice) ----------------
     out["gp"] = gp_block(fif, synth, spec, lm, r_max, m, args.gp_samples, dev, stream, hbm_peak)
