@@ -194,6 +194,25 @@ def test_trace_factor_field(F):
     _, met_full, _, _ = full.query(torch.from_numpy(poses).cuda(), F.Q_TRACE | F.Q_WORLD)
     torch.cuda.synchronize()
     assert np.all(np.abs(met[:, 0].cpu().numpy() - met_full[:, 0].cpu().numpy()) <= t_tr)
+    # a batch of 40,000 poses (many groups of 32 and a ragged last one) with a non-finite pose,
+    # one outside the lattice and one with an unnormalised quaternion: status bits and the
+    # non-finite flag as the full query gives them, traces within the same bound
+    many = X.room_poses(40_000)
+    many[7, 0] = np.nan
+    many[100, :3] = (-3.0, 50.0, 1.0)
+    many[39_999, 3:] *= 1.5
+    _, mt, _, stt = tf.query(torch.from_numpy(many).cuda())
+    ff, mf, _, stf = full.query(torch.from_numpy(many).cuda(), F.Q_TRACE | F.Q_WORLD)
+    torch.cuda.synchronize()
+    mask = F.POSE_OUTSIDE | F.POSE_QUAT | F.POSE_NAN
+    np.testing.assert_array_equal(stt.cpu().numpy() & mask, stf.cpu().numpy() & mask)
+    assert stt[7].item() & F.POSE_NAN and stt[100].item() & F.POSE_OUTSIDE and stt[39_999].item() & F.POSE_QUAT
+    a, b = mt[:, 0].cpu().numpy(), mf[:, 0].cpu().numpy()
+    assert np.isnan(a[7]) and np.isnan(b[7])
+    ok = np.isfinite(b)
+    # both are within the FP32 metric bound of the exact trace, so within twice it of each other
+    t_many, _, _ = X.metric_tolerances(X.unpack21(ff.cpu().numpy()[ok].astype(np.float64)), X.TAU_F32)
+    assert np.all(np.abs(a[ok] - b[ok]) <= 2 * t_many)
 
 
 @pytest.mark.parametrize("case", ["tall_room", "warehouse"])
