@@ -422,6 +422,22 @@ def serving_run(fif, serve, field, reqs, rate, seed):
             "peak_inflight_bytes": srv.peak_bytes, **serve.latency_stats(res)}
 
 
+def serving_sweep(fif, serve, synth, scene, field, field16, n_requests):
+    """Poisson request streams at 2k-50k requests/s (8-4096 poses each) on the fp32 and bf16
+    fields; the 20k fp32 run is the headline p99."""
+    reqs = synth.request_stream(3, n_requests, scene)
+    sweep = {}
+    for sname, sfield, bpp in (("f32", field, 6720), ("bf16", field16, 3360)):
+        for rate in (2_000.0, 5_000.0, 10_000.0, 20_000.0, 50_000.0):
+            r = serving_run(fif, serve, sfield, reqs, rate, 4)
+            r["effective_gather_gbs"] = r["served_queries_per_s"] * bpp / 1e9
+            sweep[f"{sname}@{int(rate)}"] = r
+    return {"serving": sweep["f32@20000"],
+            "serving_sweep": {k: {kk: v[kk] for kk in ("served_queries_per_s", "p50_ms", "p99_ms",
+                                                         "effective_gather_gbs", "batches")}
+                              for k, v in sweep.items()}}
+
+
 def serve_arrivals(seed, count, rate):
     from paper_2008_03324_gb300 import synth
     return synth.poisson_arrivals(seed, count, rate)
@@ -462,7 +478,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--poses", type=int, default=1 << 22)
-    ap.add_argument("--phase", default="all", choices=["all", "query", "build", "gp", "pointcloud", "trace"],
+    ap.add_argument("--phase", default="all", choices=["all", "query", "build", "gp", "pointcloud", "trace", "serve"],
                     help="build: time only the build; query: build once untimed, time only the query; "
                          "gp: only the GP-visibility field block")
     ap.add_argument("--gp-samples", type=int, default=70, help="GP sample axes N_s of the GP block")
@@ -509,6 +525,20 @@ def main():
             print(json.dumps({"metric": "GP-field queries/s", "value": gpo["queries_per_s"], "unit": "queries/s",
                               "n_gpus": ws, "config": {"workload": WORKLOAD, "lattice": list(spec.dims)},
                               "gp": gpo}), flush=True)
+        return 0
+    if args.phase == "serve":
+        # the serving sweep alone, on fp32 and bf16 fields of the warehouse map
+        sf = fif.Field(spec.origin, spec.res, spec.dims, params)
+        sf16 = fif.Field(spec.origin, spec.res, spec.dims, params, storage=fif.STORAGE_BF16)
+        sws = torch.empty(fif.build_workspace_bytes(sf.c, lm.shape[0]), dtype=torch.uint8, device=dev)
+        fif.build(sf.c, lm, sws)
+        fif.build(sf16.c, lm, sws)
+        del sws
+        so = serving_sweep(fif, serve, synth, scene, sf, sf16, args.serve_requests)
+        if rank == 0:
+            print(json.dumps({"metric": "served pose-FIM queries/s + p99 latency", "unit": "queries/s",
+                              "value": so["serving"]["served_queries_per_s"], "n_gpus": ws,
+                              "config": {"workload": WORKLOAD, "lattice": list(spec.dims)}, **so}), flush=True)
         return 0
     if args.phase == "trace":
         # the positional trace factor alone: build, then the world-frame trace query of the poses
@@ -803,17 +833,7 @@ def main():
     if rank == 0 and args.serve_requests > 0:
         # Poisson request streams at 2k-50k requests/s (8-4096 poses each) on the fp32 and bf16
         # fields; the 20k fp32 run is the headline p99
-        reqs = synth.request_stream(3, args.serve_requests, scene)
-        sweep = {}
-        for sname, sfield, bpp in (("f32", field, 6720), ("bf16", field16, 3360)):
-            for rate in (2_000.0, 5_000.0, 10_000.0, 20_000.0, 50_000.0):
-                r = serving_run(fif, serve, sfield, reqs, rate, 4)
-                r["effective_gather_gbs"] = r["served_queries_per_s"] * bpp / 1e9
-                sweep[f"{sname}@{int(rate)}"] = r
-        out["serving"] = sweep["f32@20000"]
-        out["serving_sweep"] = {k: {kk: v[kk] for kk in ("served_queries_per_s", "p50_ms", "p99_ms",
-                                                          "effective_gather_gbs", "batches")}
-                                for k, v in sweep.items()}
+        out.update(serving_sweep(fif, serve, synth, scene, field, field16, args.serve_requests))
     del field16
     if rank == 0:
         out["method_accuracy"] = method_accuracy(fif, synth, dev)
