@@ -27,7 +27,7 @@
 // slot of 32 axes holds r <= 16 samples, it takes q = 32 / r landmarks per pass instead of one
 // (lane l: axis 32 k + l mod r, landmark l / r), and the epilogue adds the q partial sums of an
 // axis in a fixed order; at N_s = 70 this removes the 26 idle lanes of the third slot.  Blocks
-// of about 64 pairs are summed in registers and merged into Kahan pairs in shared memory.
+// of about 128 pairs are summed in registers and merged into Kahan pairs in shared memory.
 //
 #include "fif_common.cuh"
 #include "fif_internal.h"
@@ -48,7 +48,7 @@ constexpr int kGbWarps = 16;                   // a 4 x 2 x 2 brick of nodes, on
 constexpr int kGbThreads = kGbWarps * 32;
 constexpr int kGbTile = 256;
 constexpr int kGbSlots = 3;
-constexpr int kGbBlock = 64;                   // pairs per register block (Kahan granularity)
+constexpr int kGbBlock = 128;                  // pairs per register block (Kahan granularity)
 constexpr int kGbMaxRuns = 2048;
 constexpr int kGbMom = 15;
 
