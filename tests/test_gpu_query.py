@@ -194,7 +194,7 @@ def test_query_host_matches_device(F, storage):
     fim, met, sg, st = run(F, field, poses)
     h_poses = torch.from_numpy(np.ascontiguousarray(poses, np.float32)).pin_memory()
     cs = torch.cuda.Stream()
-    for chunk in (700, 4096):
+    for chunk in (64, 700, 4096):      # 64: about 40 pieces reuse each staging buffer
         staging = torch.empty(F.query_host_staging_bytes(chunk), dtype=torch.uint8, device="cuda")
         h_fim = torch.full((len(poses), 21), np.nan, dtype=torch.float32).pin_memory()
         h_met = torch.full((len(poses), 3), np.nan, dtype=torch.float64).pin_memory()
