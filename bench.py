@@ -799,9 +799,15 @@ def main():
         loss.backward()
 
     ttj = time_events(traj_step, 10, 3, stream)
+    # the same step captured once in a CUDA graph and replayed (traj.GraphedObjective)
+    gobj = traj.GraphedObjective(ctrl_t, yaw_t, B_t, field08)
+    ttg = time_events(lambda: gobj.step(), 10, 3, stream)
     out["trajopt"] = {"trajectories": 256, "samples": 128, "poses": 256 * 128, "v_alpha": 0.8,
                       "ms_forward_backward": float(np.mean(ttj)),
-                      "poses_per_s": 256 * 128 / (float(np.mean(ttj)) * 1e-3)}
+                      "poses_per_s": 256 * 128 / (float(np.mean(ttj)) * 1e-3),
+                      "ms_forward_backward_graphed": float(np.mean(ttg)),
+                      "poses_per_s_graphed": 256 * 128 / (float(np.mean(ttg)) * 1e-3)}
+    del gobj
 
     # ---------------- large map: 2M landmarks, 400 x 400 x 80 nodes (12.8M), r_max 12 m ----------------
     if not args.no_large:

@@ -60,3 +60,46 @@ def potential_cost_objective(ctrl: torch.Tensor, yaw_ctrl: torch.Tensor, basis: 
     met, sg, st = fif.FifQuery.apply(t.contiguous(), phi, quat.contiguous(), field, flags)
     cost = fif.InfoCost.apply(met, column, eps, k_q)
     return cost.sum(), phi, met
+
+
+class GraphedObjective:
+    """neg_logdet_objective and its backward pass captured once in a CUDA graph, for the many
+    evaluations of one trajectory batch that an optimiser makes: the batch shape, the field and
+    the flags are fixed at capture; each step() copies new control points (and yaws) into the
+    captured inputs and replays the graph, which issues the same kernels (the B-spline map, the
+    library's query and adjoint, the reductions) without the per-kernel launch cost of the host.
+    After step(), `loss`, `ctrl_grad` and `phi_grad` hold the results (static tensors, overwritten
+    by the next step)."""
+
+    def __init__(self, ctrl: torch.Tensor, yaw_ctrl: torch.Tensor, basis: torch.Tensor, field: fif.Field,
+                 flags: int = fif.Q_METRICS, warmup: int = 3):
+        self.ctrl = ctrl.detach().clone().requires_grad_(True)
+        self.yaw = yaw_ctrl.detach().clone()
+        self.basis = basis.detach().clone()
+        self.field = field
+        side = torch.cuda.Stream(device=self.ctrl.device)
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):          # warm-up off the capture (allocator, lazy init)
+            for _ in range(warmup):
+                self.ctrl.grad = None
+                loss, _, _, _ = neg_logdet_objective(self.ctrl, self.yaw, self.basis, field, flags)
+                loss.backward()
+        torch.cuda.current_stream().wait_stream(side)
+        self.ctrl.grad = None
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.loss, self.phi, self.met, self.sign = neg_logdet_objective(self.ctrl, self.yaw, self.basis,
+                                                                           field, flags)
+            self.loss.backward()
+        self.ctrl_grad = self.ctrl.grad
+        self.phi_grad = self.phi.grad
+
+    def step(self, ctrl: torch.Tensor = None, yaw_ctrl: torch.Tensor = None):
+        """Replay with new inputs (None keeps the previous ones); returns (loss, d loss / d ctrl)."""
+        with torch.no_grad():
+            if ctrl is not None:
+                self.ctrl.copy_(ctrl)
+            if yaw_ctrl is not None:
+                self.yaw.copy_(yaw_ctrl)
+        self.graph.replay()
+        return self.loss, self.ctrl_grad

@@ -83,3 +83,32 @@ def test_trajectory_objective_and_gradients(F):
         cm[tt, cc, dd] -= h
         fd = (oracle_objective(cp, yaw, basis)[0] - oracle_objective(cm, yaw, basis)[0]) / (2 * h)
         assert abs(gc[tt, cc, dd] - fd) <= 1e-3 * max(abs(fd), 1e-3 * np.abs(gc_ref).max())
+
+
+def test_graphed_objective_replays_the_eager_result(F):
+    """traj.GraphedObjective (the objective and its backward captured in one CUDA graph): for two
+    different sets of control points, a replay gives bitwise the loss and the control-point and
+    so(3) gradients of the eager evaluation, and the first set's again after the second."""
+    from paper_2008_03324_gb300 import traj
+    spec = X.ROOM["grid"]
+    field = F.Field(spec.origin, spec.res, spec.dims, F.make_params(r_max=8.0, v_alpha=0.8))
+    field.coeffs.copy_(torch.from_numpy(X.pack_field(X.room_field_oracle(True))))
+    ctrl, yaw, basis = setup_batch(n_traj=16, n_ctrl=8, n_samples=32)
+    B = torch.from_numpy(basis).cuda()
+    sets = [(torch.from_numpy(ctrl).cuda(), torch.from_numpy(yaw).cuda()),
+            (torch.from_numpy(ctrl + np.float32(0.05)).cuda(), torch.from_numpy(yaw - np.float32(0.1)).cuda())]
+
+    def eager(c0, y0):
+        c = c0.clone().requires_grad_(True)
+        loss, phi, _, _ = traj.neg_logdet_objective(c, y0, B, field)
+        loss.backward()
+        return float(loss), c.grad.clone(), phi.grad.clone()
+
+    ref = [eager(c, y) for c, y in sets]
+    g = traj.GraphedObjective(sets[0][0], sets[0][1], B, field)
+    for k in (0, 1, 0):
+        loss, gc = g.step(*sets[k])
+        torch.cuda.synchronize()
+        assert F.device_error() == 0
+        assert float(loss) == ref[k][0]
+        assert torch.equal(gc, ref[k][1]) and torch.equal(g.phi_grad, ref[k][2])
