@@ -52,12 +52,25 @@ constexpr int kGbBlock = 128;                  // pairs per register block (Kaha
 constexpr int kGbMaxRuns = 2048;
 constexpr int kGbMom = 15;
 
+// a compacted in-shell landmark: the bearing u, 1/n and the products the 15 moments weight
+// (u_a u_b, u_a u_b / n^2, u_a / n), formed once by the lane that found it instead of by all 32
+// lanes of the node's warp
+struct GbPair {
+    float4 m01;     // x^2, y^2, z^2, x y
+    float4 m2w0;    // x z, y z, x^2 / n^2, y^2 / n^2
+    float4 w12;     // z^2 / n^2, x y / n^2, x z / n^2, y z / n^2
+    float4 un;      // x / n, y / n, z / n, unused
+    float4 u;       // x, y, z, 1 / n
+};
+
 template <int G>
 struct GpBuildSmem {
     float hi[kGbWarps][kGbMom * G][32];
-    float lo[kGbWarps][kGbMom * G][32];
+    // the Kahan compensation in bfloat16: it is below half an ulp of the sum, so its 8
+    // significant bits extend the sum to about 32 (and halve the space of a float32 term)
+    __nv_bfloat16 lo[kGbWarps][kGbMom * G][32];
     float4 tile[kGbSlots][kGbTile];
-    float4 list[kGbWarps][32];
+    GbPair list[kGbWarps][32];
     int2 runs[kGbMaxRuns];
     int tile_count[kGbSlots];
     int nruns;
@@ -97,10 +110,10 @@ __global__ void __launch_bounds__(kGbThreads + 32, 1) gp_build_kernel(BuildArgs 
                           a.oz + a.res * min(k0 + 1, a.nz - 1)};
 
     float* hs = &S.hi[0][0][0];
-    float* ls = &S.lo[0][0][0];
+    __nv_bfloat16* ls = &S.lo[0][0][0];
     for (int idx = tid; idx < kGbWarps * kGbMom * G * 32; idx += kGbThreads + 32) {
         hs[idx] = 0.f;
-        ls[idx] = 0.f;
+        ls[idx] = __float2bfloat16_rn(0.f);
     }
     const int* startp = reinterpret_cast<const int*>(a.ws + a.lay.start);
     const int nrows =
@@ -169,17 +182,25 @@ __global__ void __launch_bounds__(kGbThreads + 32, 1) gp_build_kernel(BuildArgs 
         accz[k] = 0.f;
     }
     float* hw = hs + warp * kGbMom * G * 32 + lane;
-    float* lw = ls + warp * kGbMom * G * 32 + lane;
+    __nv_bfloat16* lw = ls + warp * kGbMom * G * 32 + lane;
+    // Kahan step of a block sum x into (hi, compensation)
+    auto kmerge = [&](int idx, float x) {
+        const float s0 = hw[idx], c = __bfloat162float(lw[idx]);
+        const float y = x - c;
+        const float t = s0 + y;
+        lw[idx] = __float2bfloat16_rn((t - s0) - y);
+        hw[idx] = t;
+    };
     auto merge = [&]() {
 #pragma unroll
         for (int k = 0; k < G; ++k) {
 #pragma unroll
             for (int q = 0; q < 7; ++q) {
-                kahan_merge(hw, lw, (k * kGbMom + 2 * q) * 32, acc[k][q].x);
-                kahan_merge(hw, lw, (k * kGbMom + 2 * q + 1) * 32, acc[k][q].y);
+                kmerge((k * kGbMom + 2 * q) * 32, acc[k][q].x);
+                kmerge((k * kGbMom + 2 * q + 1) * 32, acc[k][q].y);
                 acc[k][q] = make_float2(0.f, 0.f);
             }
-            kahan_merge(hw, lw, (k * kGbMom + 14) * 32, accz[k]);
+            kmerge((k * kGbMom + 14) * 32, accz[k]);
             accz[k] = 0.f;
         }
     };
@@ -207,7 +228,7 @@ __global__ void __launch_bounds__(kGbThreads + 32, 1) gp_build_kernel(BuildArgs 
     int inblock = 0;
     unsigned long long in_pairs = 0, cand = 0;
     bool ok = true;
-    float4* list = S.list[warp];
+    GbPair* list = S.list[warp];
     for (int it = 0;; ++it) {
         const int slot = it % kGbSlots;
         const uint32_t par = (uint32_t)((it / kGbSlots) & 1);
@@ -235,22 +256,26 @@ __global__ void __launch_bounds__(kGbThreads + 32, 1) gp_build_kernel(BuildArgs 
                 const unsigned mask = __ballot_sync(0xffffffffu, in);
                 if (in) {
                     const float r = rsqrtf(n2);
-                    list[__popc(mask & ((1u << lane) - 1u))] = make_float4(dx * r, dy * r, dz * r, r);
+                    const float x = dx * r, y = dy * r, z = dz * r, w2 = r * r;
+                    GbPair& P = list[__popc(mask & ((1u << lane) - 1u))];
+                    const float xx = x * x, yy = y * y, zz = z * z, xy = x * y, xz = x * z, yz = y * z;
+                    P.m01 = make_float4(xx, yy, zz, xy);
+                    P.m2w0 = make_float4(xz, yz, xx * w2, yy * w2);
+                    P.w12 = make_float4(zz * w2, xy * w2, xz * w2, yz * w2);
+                    P.un = make_float4(x * r, y * r, z * r, 0.f);
+                    P.u = make_float4(x, y, z, r);
                 }
                 __syncwarp();
                 const int nin = __popc(mask);
 #pragma unroll 2
                 for (int l = 0; l < (main_slots ? nin : 0); ++l) {
-                    const float4 L = list[l];
-                    const float x = L.x, y = L.y, z = L.z, in_ = L.w, w2 = L.w * L.w;
-                    const float2 xy = make_float2(x, y);
-                    const float2 m0 = mul2(xy, xy);                               // xx, yy
-                    const float2 m1 = mul2(make_float2(z, x), make_float2(z, y));  // zz, xy
-                    const float2 m2 = mul2(xy, make_float2(z, z));                 // xz, yz
-                    const float2 ww = make_float2(w2, w2);
-                    const float2 X[7] = {m0, m1, m2, mul2(m0, ww), mul2(m1, ww), mul2(m2, ww),
-                                         mul2(xy, make_float2(in_, in_))};
-                    const float zi = z * in_;
+                    const GbPair& P = list[l];
+                    const float4 A = P.m01, Bq = P.m2w0, Cq = P.w12, D = P.un, U = P.u;
+                    const float x = U.x, y = U.y, z = U.z;
+                    const float2 X[7] = {make_float2(A.x, A.y), make_float2(A.z, A.w), make_float2(Bq.x, Bq.y),
+                                         make_float2(Bq.z, Bq.w), make_float2(Cq.x, Cq.y), make_float2(Cq.z, Cq.w),
+                                         make_float2(D.x, D.y)};
+                    const float zi = D.z;
                     float v[G];
                     sigmoids(x, y, z, v);
 #pragma unroll
@@ -270,21 +295,18 @@ __global__ void __launch_bounds__(kGbThreads + 32, 1) gp_build_kernel(BuildArgs 
                         const int li = l0 + jq;
                         const bool act = jq < qq && li < nin;   // idle lanes add zero weights
                         {
-                            const float4 L = list[act ? li : 0];
-                            const float x = L.x, y = L.y, z = L.z, in_ = L.w, w2 = L.w * L.w;
-                            const float2 xy = make_float2(x, y);
-                            const float2 m0 = mul2(xy, xy);
-                            const float2 m1 = mul2(make_float2(z, x), make_float2(z, y));
-                            const float2 m2 = mul2(xy, make_float2(z, z));
-                            const float2 ww = make_float2(w2, w2);
-                            const float2 X[7] = {m0, m1, m2, mul2(m0, ww), mul2(m1, ww), mul2(m2, ww),
-                                                 mul2(xy, make_float2(in_, in_))};
+                            const GbPair& P = list[act ? li : 0];
+                            const float4 A = P.m01, Bq = P.m2w0, Cq = P.w12, D = P.un, U = P.u;
+                            const float x = U.x, y = U.y, z = U.z;
+                            const float2 X[7] = {make_float2(A.x, A.y), make_float2(A.z, A.w), make_float2(Bq.x, Bq.y),
+                                                 make_float2(Bq.z, Bq.w), make_float2(Cq.x, Cq.y), make_float2(Cq.z, Cq.w),
+                                                 make_float2(D.x, D.y)};
                             const float arg = fmaf(nzx[k], x, fmaf(nzy[k], y, fmaf(nzz[k], z, shift)));
                             const float vk = act ? rcp_approx(1.f + ex2_approx(fminf(arg, 60.f))) : 0.f;
                             const float2 vv = make_float2(vk, vk);
 #pragma unroll
                             for (int q = 0; q < 7; ++q) acc[k][q] = fma2(vv, X[q], acc[k][q]);
-                            accz[k] = fmaf(vk, z * in_, accz[k]);
+                            accz[k] = fmaf(vk, D.z, accz[k]);
                         }
                     }
                 }
@@ -326,12 +348,12 @@ __global__ void __launch_bounds__(kGbThreads + 32, 1) gp_build_kernel(BuildArgs 
                 float t = 0.f;
                 if (lane < rr)
                     for (int j = 0; j < qq; ++j)
-                        t += hw[(k * kGbMom + m) * 32 + j * rr] - lw[(k * kGbMom + m) * 32 + j * rr];
+                        t += hw[(k * kGbMom + m) * 32 + j * rr] - __bfloat162float(lw[(k * kGbMom + m) * 32 + j * rr]);
                 mo[m] = t;
             }
         } else {
 #pragma unroll
-            for (int m = 0; m < kGbMom; ++m) mo[m] = hw[(k * kGbMom + m) * 32] - lw[(k * kGbMom + m) * 32];
+            for (int m = 0; m < kGbMom; ++m) mo[m] = hw[(k * kGbMom + m) * 32] - __bfloat162float(lw[(k * kGbMom + m) * 32]);
         }
         const bool live = ok && g < a.gp_ns;
 #pragma unroll
