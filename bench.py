@@ -697,8 +697,9 @@ def main():
     h_sg = torch.empty(m, dtype=torch.int8).pin_memory()
     h_st = torch.empty(m, dtype=torch.int32).pin_memory()
 
-    # fif_query_host: chunks of E2E_CHUNK poses double-buffered through device staging, copies on a
-    # second stream overlapping the queries
+    # fif_query_host on page-locked buffers: the query reads the poses from and writes the outputs
+    # to host memory in place over the host link (pageable buffers would go through the staged
+    # chunks of E2E_CHUNK poses, copies on a second stream)
     copy_stream = torch.cuda.Stream(device=dev)
     staging = torch.empty(fif.query_host_staging_bytes(E2E_CHUNK), dtype=torch.uint8, device=dev)
 
@@ -712,8 +713,9 @@ def main():
     e2e_ms = dist.max_over_ranks(float(np.mean(te)), dev)
     e2e = {"value": m * ws / (e2e_ms * 1e-3), "unit": "queries/s", "h2d_bytes_per_step": m * 28,
            "d2h_bytes_per_step": m * (84 + 24 + 1 + 4), "ms_per_step": e2e_ms,
-           "api": (f"fif_query_host, pinned host buffers, chunks of {E2E_CHUNK} poses; the same outputs as the "
-                   "timed step (FIM, trace / log|det| / lambda_min, sign, status)")}
+           "api": ("fif_query_host, page-locked host buffers queried in place (poses read and outputs written "
+                   "over the host link by the query kernel); the same outputs as the timed step (FIM, trace / "
+                   "log|det| / lambda_min, sign, status)")}
     del staging
 
     # ---------------- point-cloud baseline (all 200k landmarks) ----------------

@@ -338,7 +338,12 @@ FIF_API size_t fif_query_host_staging_bytes(int64_t chunk);
  * those fif_query gives it.  Asynchronous: the host outputs are complete once `stream` has
  * completed (it waits for the last copy); h_poses and the outputs must stay valid until then.
  * copy_stream must differ from stream (FIF_EINVAL otherwise).  m = 0 returns FIF_OK and
- * touches nothing. */
+ * touches nothing.
+ * When h_poses and every non-NULL output are page-locked memory the device can address
+ * (cudaHostAlloc / cudaMallocHost memory, mapped on every system with unified addressing), the
+ * arguments are checked as above and then fif_query runs on those buffers in place: its kernels
+ * read the poses from host memory and write the results there over the host link, with no
+ * staging copies (d_staging and copy_stream are not used; the results are the same). */
 FIF_API int32_t fif_query_host(const fif_field* field, const float* h_poses, int64_t m, int32_t flags,
                                float* h_fim, double* h_metrics, int8_t* h_sign, int32_t* h_status,
                                int64_t chunk, void* d_staging, size_t staging_bytes, fif_stream_t stream,

@@ -371,6 +371,28 @@ int32_t fif_query_host(const fif_field* field, const float* h_poses, int64_t m, 
     if (chunk <= 0 || !d_staging || stream == copy_stream) return FIF_EINVAL;
     if (staging_bytes < fif_query_host_staging_bytes(chunk)) return FIF_ESIZE;
     if (reinterpret_cast<uintptr_t>(d_staging) & 15u) return FIF_EALIGN;
+    // page-locked host buffers that the device can address (cudaHostAlloc memory, mapped on any
+    // system with unified addressing): the query reads the poses from and writes the outputs to
+    // them in place over the host link, with no staging copies and no HBM traffic for the I/O
+    {
+        auto mapped = [](const void* p, void** dp) -> bool {
+            *dp = nullptr;
+            if (!p) return true;
+            cudaPointerAttributes at{};
+            if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+                cudaGetLastError();
+                return false;
+            }
+            if (at.type != cudaMemoryTypeHost || !at.devicePointer) return false;
+            *dp = at.devicePointer;
+            return true;
+        };
+        void *dp, *df, *dm, *ds, *dt;
+        if (mapped(h_poses, &dp) && mapped(h_fim, &df) && mapped(h_metrics, &dm) && mapped(h_sign, &ds) &&
+            mapped(h_status, &dt))
+            return fif_query(field, static_cast<const float*>(dp), m, flags, static_cast<float*>(df),
+                             static_cast<double*>(dm), static_cast<int8_t*>(ds), static_cast<int32_t*>(dt), stream);
+    }
     const HostStaging L = host_staging(chunk);
     unsigned char* base[2] = {static_cast<unsigned char*>(d_staging),
                               static_cast<unsigned char*>(d_staging) + L.total};

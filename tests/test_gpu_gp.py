@@ -377,21 +377,23 @@ def test_gp_build_and_query_end_to_end(F, ns):
 
 
 def test_gp_query_host_matches_device(F):
-    """fif_query_host on a GP field (N_s = 30): chunks through device staging give every pose the
-    device results bitwise."""
+    """fif_query_host on a GP field (N_s = 30): page-locked buffers queried in place, and pageable
+    ones in chunks through device staging, give every pose the device results bitwise."""
     field = uploaded(F, 30)
     poses = X.room_poses(300)
     fim, met, sg, st = run(F, field, poses)
-    h = torch.from_numpy(np.ascontiguousarray(poses, np.float32)).pin_memory()
-    h_fim = torch.empty(len(poses), 21, dtype=torch.float32).pin_memory()
-    h_met = torch.empty(len(poses), 3, dtype=torch.float64).pin_memory()
-    h_sg = torch.empty(len(poses), dtype=torch.int8).pin_memory()
-    h_st = torch.empty(len(poses), dtype=torch.int32).pin_memory()
     staging = torch.empty(F.query_host_staging_bytes(128), dtype=torch.uint8, device="cuda")
-    F.query_host(field.c, h, F.Q_METRICS, h_fim, h_met, h_sg, h_st, chunk=128, staging=staging,
-                 copy_stream=torch.cuda.Stream())
-    torch.cuda.current_stream().synchronize()
-    np.testing.assert_array_equal(h_fim.numpy(), fim)
-    np.testing.assert_array_equal(h_met.numpy(), met)
-    np.testing.assert_array_equal(h_sg.numpy(), sg)
-    np.testing.assert_array_equal(h_st.numpy(), st)
+    for pinned in (True, False):
+        pin = (lambda t: t.pin_memory()) if pinned else (lambda t: t)
+        h = pin(torch.from_numpy(np.ascontiguousarray(poses, np.float32)))
+        h_fim = pin(torch.empty(len(poses), 21, dtype=torch.float32))
+        h_met = pin(torch.empty(len(poses), 3, dtype=torch.float64))
+        h_sg = pin(torch.empty(len(poses), dtype=torch.int8))
+        h_st = pin(torch.empty(len(poses), dtype=torch.int32))
+        F.query_host(field.c, h, F.Q_METRICS, h_fim, h_met, h_sg, h_st, chunk=128, staging=staging,
+                     copy_stream=torch.cuda.Stream())
+        torch.cuda.current_stream().synchronize()
+        np.testing.assert_array_equal(h_fim.numpy(), fim)
+        np.testing.assert_array_equal(h_met.numpy(), met)
+        np.testing.assert_array_equal(h_sg.numpy(), sg)
+        np.testing.assert_array_equal(h_st.numpy(), st)

@@ -185,8 +185,9 @@ def test_metrics_of_the_returned_fim(F, storage):
 
 @pytest.mark.parametrize("storage", [0, 1])
 def test_query_host_matches_device(F, storage):
-    """fif_query_host (pinned host buffers, chunks double-buffered through device staging, copies
-    on a second stream) gives every pose exactly the results fif_query gives it on the device:
+    """fif_query_host (page-locked host buffers queried in place; pageable ones in chunks
+    double-buffered through device staging, copies on a second stream) gives every pose exactly
+    the results fif_query gives it on the device:
     a ragged last chunk, a chunk larger than the batch, a subset of the outputs, the empty
     batch and the argument checks."""
     field = uploaded_room_field(F, storage=storage)
@@ -194,13 +195,16 @@ def test_query_host_matches_device(F, storage):
     fim, met, sg, st = run(F, field, poses)
     h_poses = torch.from_numpy(np.ascontiguousarray(poses, np.float32)).pin_memory()
     cs = torch.cuda.Stream()
-    for chunk in (64, 700, 4096):      # 64: about 40 pieces reuse each staging buffer
+    # page-locked buffers are queried in place; pageable ones go through the staged chunks
+    for pinned, chunk in ((True, 700), (False, 64), (False, 700), (False, 4096)):
+        pin = (lambda t: t.pin_memory()) if pinned else (lambda t: t)
+        hp = h_poses if pinned else h_poses.clone()
         staging = torch.empty(F.query_host_staging_bytes(chunk), dtype=torch.uint8, device="cuda")
-        h_fim = torch.full((len(poses), 21), np.nan, dtype=torch.float32).pin_memory()
-        h_met = torch.full((len(poses), 3), np.nan, dtype=torch.float64).pin_memory()
-        h_sg = torch.zeros(len(poses), dtype=torch.int8).pin_memory()
-        h_st = torch.full((len(poses),), -1, dtype=torch.int32).pin_memory()
-        F.query_host(field.c, h_poses, F.Q_METRICS, h_fim, h_met, h_sg, h_st, chunk=chunk, staging=staging,
+        h_fim = pin(torch.full((len(poses), 21), np.nan, dtype=torch.float32))
+        h_met = pin(torch.full((len(poses), 3), np.nan, dtype=torch.float64))
+        h_sg = pin(torch.zeros(len(poses), dtype=torch.int8))
+        h_st = pin(torch.full((len(poses),), -1, dtype=torch.int32))
+        F.query_host(field.c, hp, F.Q_METRICS, h_fim, h_met, h_sg, h_st, chunk=chunk, staging=staging,
                      copy_stream=cs)
         torch.cuda.current_stream().synchronize()
         assert F.device_error() == 0
