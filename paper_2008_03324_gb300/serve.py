@@ -4,11 +4,11 @@ Planner requests (RRT* edges, trajectory samples: 8-4096 poses each) arrive over
 loop admits a request when a slot is free and its bytes fit the in-flight memory budget, and
 the request then lives on the device: its poses go into a device ring of pose slots (placed at
 admission; copied while every stream is busy, on an upload stream that overlaps the batches in
-flight, or else by the launch that takes them), the next batch queries the ring in place
-(one fif_query per contiguous run of requests) and writes the metrics into the same slots, and
-one device-to-host copy per run returns them.  Up to `streams` batches are in flight on
-separate CUDA streams, so requests that arrive while a batch runs join the next one.  Completion is detected by polling CUDA events against a deadline (no blocking
-waits).  Every result is independent of the batch it travelled in: the query of a pose
+flight, or else by the launch that takes them), and the next batch queries the ring in place
+(one fif_query per contiguous run of requests), writing the metrics of each slot straight into
+its page-locked host mirror.  Up to `streams` batches are in flight on separate CUDA streams,
+so requests that arrive while a batch runs join the next one.  Completion is detected by
+polling CUDA events against a deadline (no blocking waits).  Every result is independent of the batch it travelled in: the query of a pose
 depends on that pose only.
 
 The scheduler (`Scheduler`) is separate from the executor that owns the streams and buffers
@@ -104,14 +104,15 @@ def contiguous_runs(offsets, lengths):
 
 
 class CudaExecutor:
-    """Request state resident on the device: a ring of pose slots in device memory (poses in,
-    metrics / sign / status out) with a pinned host mirror.  A request's poses are placed in its
+    """Request state resident on the device: a ring of pose slots in device memory with a
+    page-locked host mirror, into which the query writes each request's metrics, sign and status
+    directly (device-addressable host memory, mapped on every system with unified addressing).  A request's poses are placed in its
     ring range when it is admitted; while every stream is busy, the placed ranges are copied to
     the device on an upload stream (once enough poses wait), so that they are there when a
     stream frees; otherwise the launch that takes them copies them on its own stream.  A batch
     is one fif_query per contiguous run of ring ranges (one, or
-    two where the batch wraps), reading and writing the ring in place, and one device-to-host
-    copy per run brings its outputs back.  `n_streams` batches are in flight at once."""
+    two where the batch wraps), reading the ring in place.  `n_streams` batches are in flight at
+    once."""
 
     def __init__(self, fld, max_batch_poses: int, n_streams: int = 2, flags=None, ring_poses: int = 0):
         import torch
@@ -125,9 +126,6 @@ class CudaExecutor:
         self.ring = RequestRing(cap)
         dev = fld.coeffs.device
         self.d_pose = torch.empty(cap, 7, dtype=torch.float32, device=dev)
-        self.d_met = torch.empty(cap, 3, dtype=torch.float64, device=dev)
-        self.d_sg = torch.empty(cap, dtype=torch.int8, device=dev)
-        self.d_st = torch.empty(cap, dtype=torch.int32, device=dev)
         self.h_pose = torch.empty(cap, 7, dtype=torch.float32, pin_memory=True)
         self.h_met = torch.empty(cap, 3, dtype=torch.float64, pin_memory=True)
         self.h_sg = torch.empty(cap, dtype=torch.int8, pin_memory=True)
@@ -187,11 +185,10 @@ class CudaExecutor:
             if self.pending:
                 self._upload(s)
             for off, n in contiguous_runs(offsets, [b.shape[0] for b in batch]):
-                fif.query(self.field.c, self.d_pose[off:off + n], self.flags, None, self.d_met[off:off + n],
-                          self.d_sg[off:off + n], self.d_st[off:off + n], stream=s)
-                self.h_met[off:off + n].copy_(self.d_met[off:off + n], non_blocking=True)
-                self.h_sg[off:off + n].copy_(self.d_sg[off:off + n], non_blocking=True)
-                self.h_st[off:off + n].copy_(self.d_st[off:off + n], non_blocking=True)
+                # the outputs go straight to the page-locked mirror (device-addressable host
+                # memory): no device-to-host copy to issue or wait for
+                fif.query(self.field.c, self.d_pose[off:off + n], self.flags, None, self.h_met[off:off + n],
+                          self.h_sg[off:off + n], self.h_st[off:off + n], stream=s)
                 self.launches += 1
             self.events[slot].record(s)
 
