@@ -106,13 +106,13 @@ def contiguous_runs(offsets, lengths):
 class CudaExecutor:
     """Request state resident on the device: a ring of pose slots in device memory with a
     page-locked host mirror, into which the query writes each request's metrics, sign and status
-    directly (device-addressable host memory, mapped on every system with unified addressing).  A request's poses are placed in its
-    ring range when it is admitted; while every stream is busy, the placed ranges are copied to
-    the device on an upload stream (once enough poses wait), so that they are there when a
-    stream frees; otherwise the launch that takes them copies them on its own stream.  A batch
-    is one fif_query per contiguous run of ring ranges (one, or
-    two where the batch wraps), reading the ring in place.  `n_streams` batches are in flight at
-    once."""
+    directly (device-addressable host memory, mapped on every system with unified addressing).
+    A request's poses are placed in its ring range when it is admitted; while every stream is
+    busy, the placed ranges are copied to the device on an upload stream (once enough poses
+    wait), so that they are there when a stream frees; otherwise the launch that takes them
+    copies them on its own stream.  A batch is one fif_query per contiguous run of ring ranges
+    (one, or two where the batch wraps), reading the ring in place.  `n_streams` batches are in
+    flight at once."""
 
     def __init__(self, fld, max_batch_poses: int, n_streams: int = 2, flags=None, ring_poses: int = 0):
         import torch
