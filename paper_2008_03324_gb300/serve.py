@@ -52,6 +52,7 @@ class RequestRing:
     def __init__(self, capacity: int):
         self.cap = int(capacity)
         self.live = deque()      # [offset, length, released] in admission order
+        self.by_off = {}         # offset -> its entry in `live`
         self.tail = 0
 
     def alloc(self, n: int):
@@ -73,17 +74,15 @@ class RequestRing:
                     off = self.tail
                 else:
                     return None
-        self.live.append([off, n, False])
+        e = [off, n, False]
+        self.live.append(e)
+        self.by_off[off] = e
         self.tail = off + n
         return off
 
     def release(self, off: int):
-        for e in self.live:
-            if e[0] == off and not e[2]:
-                e[2] = True
-                break
-        else:
-            raise KeyError(f"no live range at {off}")
+        e = self.by_off.pop(off)          # KeyError: no live range there
+        e[2] = True
         while self.live and self.live[0][2]:
             self.live.popleft()
 
